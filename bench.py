@@ -1,0 +1,324 @@
+"""Benchmark of the semisort hot path on GB300.
+
+Workload (one "step" = one semisort_= call over one n = 10^9 batch):
+  semisort_= on n = 10^9 records (uint64 key, uint64 value = index); steps
+  cycle over the ten key distributions of the paper's Table 2 uniform/Zipf
+  rows: uniform with exactly {10, 10^3, 10^5, 10^7, 10^9} distinct keys and
+  Zipf s in {0.6, 0.8, 1.0, 1.2, 1.5} over 10^9 ranks (synthetic, seeded).
+  Inputs are device resident and larger than L2, so no flush is needed.
+
+Prints one JSON line (rank 0).  `--impl reference` times the CPU oracle (the
+plain stable sort that defines a valid output) on a bounded sample instead.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import math
+import os
+import statistics
+import subprocess
+import sys
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+N_DEFAULT = 10**9
+DISTS = [("uniform", 10), ("uniform", 10**3), ("uniform", 10**5), ("uniform", 10**7), ("uniform", 10**9),
+         ("zipf", 0.6), ("zipf", 0.8), ("zipf", 1.0), ("zipf", 1.2), ("zipf", 1.5)]
+SEED = 0x5EED0002
+METRIC = "semisort Grecords/s & HBM roofline % at n=1e9; learned/batched vs plain form"
+UNIT = "Grecords/s"
+
+
+def dist_name(d):
+    return f"{d[0]}-{d[1]:g}"
+
+
+def load_peaks():
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
+            p = json.load(f)
+        return float(p["hbm_gbs"]), "measured"
+    except Exception:
+        return 6800.0, "fallback"
+
+
+class Clocks:
+    """nvidia-smi sampling during the timed region."""
+
+    def __init__(self, gpu_index: int):
+        self.proc = None
+        self.path = os.path.join(ROOT, "gpurun_out", f"clocks_rank{gpu_index}.csv")
+        self.gpu = gpu_index
+
+    def start(self):
+        try:
+            os.makedirs(os.path.dirname(self.path), exist_ok=True)
+            self.f = open(self.path, "w")
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", "-i", str(self.gpu),
+                 "--query-gpu=index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+                 "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+                 "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap",
+                 "--format=csv,noheader,nounits", "-lms", "200"], stdout=self.f, stderr=subprocess.DEVNULL)
+        except Exception:
+            self.proc = None
+
+    def stop(self):
+        if self.proc is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except Exception:
+            self.proc.kill()
+        self.f.close()
+        sm, mx, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for line in open(self.path):
+            parts = [p.strip() for p in line.split(",")]
+            if len(parts) < 9:
+                continue
+            try:
+                sm.append(float(parts[1]))
+                mx.append(float(parts[2]))
+            except ValueError:
+                continue
+            for nm, v in zip(names, parts[5:9]):
+                if v.lower() == "active":
+                    reasons.add(nm)
+        return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": max(mx) if mx else None,
+                "reasons": sorted(reasons), "samples": len(sm)}
+
+
+def make_keys(sg, d, n, out):
+    kind, p = d
+    if kind == "uniform":
+        return sg.uniform_exact(SEED, n, int(p), out=out)
+    return sg.zipf(SEED, n, float(p), N=10**9, out=out)
+
+
+def cpu_oracle_sample(sample_n: int, dists) -> dict:
+    """Time the oracle (the stable sort that defines a valid semisort_=
+    output) on the host cores, on a bounded sample of each distribution."""
+    import numpy as np
+
+    import oracle
+    import synth
+    oracle.build()
+    total_n, total_t = 0, 0.0
+    for d in dists:
+        keys = synth.uniform_exact(SEED, N_DEFAULT, int(d[1]), 0, sample_n) if d[0] == "uniform" else \
+            synth.zipf(SEED, sample_n, float(d[1]), N=10**9)
+        vals = np.arange(sample_n, dtype=np.uint64)
+        t0 = time.perf_counter()
+        oracle.stable_sort(keys, vals)
+        total_t += time.perf_counter() - t0
+        total_n += sample_n
+    return {"value": total_n / total_t / 1e9, "unit": UNIT, "cores": 1, "kind": "oracle",
+            "sample": f"first {sample_n} records of {', '.join(dist_name(d) for d in dists)} "
+                      f"(same generators and seed as the GPU workload); std::stable_sort, 1 thread"}
+
+
+def run_reference(args, rank, world):
+    if rank != 0:
+        return 0
+    dists = DISTS[5:10:2] if args.quick else [DISTS[3], DISTS[8]]
+    sample_n = args.ref_sample
+    t_steps = []
+    for i in range(args.warmup + args.steps):
+        cb = cpu_oracle_sample(sample_n, [dists[i % len(dists)]])
+        if i >= args.warmup:
+            t_steps.append(sample_n / (cb["value"] * 1e9))
+    total_t = sum(t_steps)
+    value = args.steps * sample_n / total_t / 1e9
+    line = {"impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1000 * total_t / args.steps,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "u64", "data": "synthetic",
+            "config": {"workload": f"semisort_equal oracle (std::stable_sort) on {sample_n}-record samples of "
+                                   f"{', '.join(dist_name(d) for d in dists)}"},
+            "cpu_baseline": {"value": value, "unit": UNIT, "cores": 1, "kind": "oracle",
+                             "sample": f"{sample_n} records per step"},
+            "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line))
+    return 0
+
+
+def alg_bytes(st: dict) -> int:
+    """Compulsory bytes of the method's passes for one call (u64 key + u64
+    value): per record and distribution level 8 B (count: key) + 32 B
+    (distribute: read and write key and value); per refined or copied record
+    32 B (read and write)."""
+    dist = sum(st.get(f"dist_l{i}", 0) for i in range(4))
+    return 40 * dist + 32 * st.get("refined", 0) + 32 * st.get("copied", 0)
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=10)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--n", type=int, default=N_DEFAULT)
+    ap.add_argument("--ref-sample", type=int, default=1 << 24)
+    ap.add_argument("--cpu-sample", type=int, default=1 << 24)
+    ap.add_argument("--e2e-steps", type=int, default=3)
+    ap.add_argument("--quick", action="store_true", help="small smoke configuration (not a bench number)")
+    args = ap.parse_args()
+
+    rank = int(os.environ.get("RANK", "0"))
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+
+    if args.impl == "reference":
+        return run_reference(args, rank, world)
+
+    import torch
+    import torch.distributed as dist
+
+    import paper_2304_10078_gb300 as ss
+    import synth.gpu as sg
+
+    torch.cuda.set_device(local)
+    if world > 1:
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+    ss.lib()
+    n = args.n
+    dists = DISTS
+    # device-resident inputs: one key array per distribution, one value array
+    keys = []
+    vals = sg.iota(n)
+    for d in dists:
+        keys.append(make_keys(sg, d, n, None))
+    torch.cuda.synchronize()
+    kout = torch.empty(n, dtype=torch.uint64, device="cuda")
+    vout = torch.empty(n, dtype=torch.uint64, device="cuda")
+    opt = ss.make_options(seed=1, flags=ss.FLAG_PHASE_TIMING)
+    ws = ss.alloc_workspace(ss.OP_EQUAL, keys[0], vals, opt)
+    stream = torch.cuda.current_stream()
+
+    def step(i):
+        ss.semisort_equal(keys[i % len(dists)], vals, keys_out=kout, vals_out=vout, workspace=ws, options=opt)
+
+    for i in range(args.warmup):
+        step(i)
+    torch.cuda.synchronize()
+    assert ss.last_device_error(ws) == 0
+
+    per_dist = {dist_name(d): [] for d in dists}
+    dominant, dom_bytes, alg_total = [], [], 0
+    launches = 0
+    clocks = Clocks(local)
+    if world > 1:
+        dist.barrier()
+    torch.cuda.synchronize()
+    clocks.start()
+    ev0 = torch.cuda.Event(enable_timing=True)
+    ev1 = torch.cuda.Event(enable_timing=True)
+    ev0.record(stream)
+    for i in range(args.steps):
+        e_a = torch.cuda.Event(enable_timing=True)
+        e_b = torch.cuda.Event(enable_timing=True)
+        e_a.record(stream)
+        step(i)
+        e_b.record(stream)
+        launches += ss.kernel_launches()
+        # per-kernel CUDA events recorded by the library on this stream
+        ph = dict()
+        for name, ms in ss.phase_times():
+            ph[name] = ph.get(name, 0.0) + ms
+        st = ss.stats(ws)
+        alg_total += alg_bytes(st)
+        dominant.append(ph.get("distribute.L0", float("nan")))
+        dom_bytes.append(32 * st.get("dist_l0", 0))
+        e_b.synchronize()
+        per_dist[dist_name(dists[i % len(dists)])].append(e_a.elapsed_time(e_b))
+    ev1.record(stream)
+    torch.cuda.synchronize()
+    clk = clocks.stop()
+    elapsed_ms = ev0.elapsed_time(ev1)
+    if world > 1:
+        t = torch.tensor([elapsed_ms], device="cuda")
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        elapsed_ms = float(t.item())
+    assert ss.last_device_error(ws) == 0
+
+    value = world * n * args.steps / (elapsed_ms / 1000.0) / 1e9
+    peak, peak_kind = load_peaks()
+    dom_ms = [t for t in dominant if t == t]
+    dom_avg = sum(dom_ms) / len(dom_ms) if dom_ms else float("nan")
+    dom_b = sum(dom_bytes) / len(dom_bytes)
+    achieved = dom_b / (dom_avg / 1000.0) / 1e9 if dom_ms else None
+    traffic = None
+    try:
+        with open(os.path.join(ROOT, "profiles", "traffic.json")) as f:
+            traffic = json.load(f).get("distribute.L0")
+    except Exception:
+        pass
+
+    # end to end: pinned host input -> device, the call, result -> pinned host
+    e2e = None
+    if rank == 0 and args.e2e_steps > 0:
+        d_e2e = dists[8]
+        hk = torch.empty(n, dtype=torch.uint64, pin_memory=True)
+        hv = torch.empty(n, dtype=torch.uint64, pin_memory=True)
+        hko = torch.empty(n, dtype=torch.uint64, pin_memory=True)
+        hvo = torch.empty(n, dtype=torch.uint64, pin_memory=True)
+        hk.copy_(keys[8], non_blocking=False)
+        hv.copy_(vals, non_blocking=False)
+        dk, dv = keys[0], keys[1]  # device staging (reuses distribution buffers)
+        opt_plain = ss.make_options(seed=1)
+        torch.cuda.synchronize()
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        for _ in range(args.e2e_steps):
+            dk.copy_(hk, non_blocking=True)
+            dv.copy_(hv, non_blocking=True)
+            ss.semisort_equal(dk, dv, keys_out=kout, vals_out=vout, workspace=ws, options=opt_plain)
+            hko.copy_(kout, non_blocking=True)
+            hvo.copy_(vout, non_blocking=True)
+        e1.record(stream)
+        torch.cuda.synchronize()
+        t = e0.elapsed_time(e1) / 1000.0
+        e2e = {"value": n * args.e2e_steps / t / 1e9, "unit": UNIT, "h2d_bytes_per_step": 16 * n,
+               "d2h_bytes_per_step": 16 * n, "workload": f"semisort_equal n={n} {dist_name(d_e2e)}"}
+        del hk, hv, hko, hvo
+
+    if rank != 0:
+        if world > 1:
+            dist.destroy_process_group()
+        return 0
+    cpu = cpu_oracle_sample(args.cpu_sample, [dists[3], dists[8]]) if args.cpu_sample else None
+    ms_step = elapsed_ms / args.steps
+    line = {
+        "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": ms_step, "higher_is_better": True, "scaling": "weak",
+        "vs_baseline": None, "dtype": "u64", "data": "synthetic",
+        "config": {"workload": f"semisort_equal n={n} (u64 key, u64 value=index), steps cycle over "
+                               + ", ".join(dist_name(d) for d in dists),
+                   "parallelism": "replicas" if world > 1 else "single GPU",
+                   "l2": "inputs (16 GB per step) larger than L2; no flush"},
+        "roofline": {"bound": "hbm", "kernel": "distribute.L0",
+                     "achieved": achieved, "peak": peak, "peak_kind": peak_kind, "unit": "GB/s",
+                     "frac": (achieved / peak) if achieved else None, "traffic": traffic,
+                     "alg_bytes_per_launch": dom_b, "avg_launch_ms": dom_avg},
+        "path_roofline": {"alg_bytes_per_step": alg_total / args.steps,
+                          "achieved_gbs": alg_total / (elapsed_ms / 1000.0) / 1e9,
+                          "frac": alg_total / (elapsed_ms / 1000.0) / 1e9 / peak},
+        "per_distribution_ms": {k: (sum(v) / len(v) if v else None) for k, v in per_dist.items()},
+        "cpu_baseline": cpu,
+        "e2e": e2e,
+        "gpu_launches": launches,
+        "clocks": clk,
+    }
+    print(json.dumps(line))
+    if world > 1:
+        dist.destroy_process_group()
+    return 0
+
+
+if __name__ == "__main__":
+    sys.exit(main())

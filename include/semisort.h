@@ -1,0 +1,162 @@
+/*
+ * semisort.h -- C ABI of the GB300 (sm_103a) semisort library.
+ *
+ * Implements the problems of Sec. 2.1 of Dong, Wu, Wang, Dhulipala, Gu, Sun,
+ * "High-Performance and Flexible Parallel Algorithms for Semisort and Related
+ * Problems" (SPAA 2023), with the three-step method of Sec. 3 (Algorithm 1):
+ * Sampling and Bucketing, Blocked Distributing, Local Refining.
+ *
+ * Conventions shared by every entry point
+ * ---------------------------------------
+ *  - Records are given as two separate device arrays (structure of arrays):
+ *    keys[n] and vals[n].  Key types: SS_U32, SS_U64, SS_U128 (16 bytes,
+ *    little-endian lo then hi, ordered as an unsigned 128-bit integer).  Value
+ *    types: SS_U32, SS_U64.
+ *  - All pointers are DEVICE pointers owned by the caller, 16-byte aligned.
+ *    The library never allocates device memory: scratch space comes from the
+ *    caller's workspace `ws` of `ws_bytes` bytes, sized by
+ *    ss_workspace_size() for the same (op, types, n, options).
+ *  - Calls are asynchronous and stream ordered on `stream` (0 = legacy
+ *    default stream).  No call synchronizes with the host; every size that
+ *    steers the recursion stays on the device, so a call can be captured in a
+ *    CUDA graph.  Workspace and outputs must not be shared by calls that may
+ *    run concurrently.
+ *  - Return values report argument errors found on the host at enqueue time.
+ *    Failures found on the device (an internal capacity limit, the recursion
+ *    depth limit) set a flag in the workspace; ss_last_device_error() reads
+ *    and clears it.  Each call resets the flag when it starts, so the flag
+ *    describes the most recent call on that workspace.  No kernel traps.
+ *  - n = 0 is valid and enqueues nothing.  n must be below 2^32 - 2^20.
+ *  - Determinism: for a fixed options.seed every output is bit-identical
+ *    across runs (the method is race-free, Sec. 2.2 and Sec. 3).
+ */
+#ifndef SEMISORT_H_
+#define SEMISORT_H_
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct CUstream_st* ss_stream_t; /* same type as cudaStream_t */
+
+typedef enum {
+  SS_OK = 0,
+  SS_ERR_INVALID_ARG = 1,         /* null/misaligned pointer, bad type, overlap */
+  SS_ERR_UNSUPPORTED = 2,         /* type combination or size not supported */
+  SS_ERR_WORKSPACE_TOO_SMALL = 3, /* ws_bytes below ss_workspace_size() */
+  SS_ERR_CAPACITY = 4,            /* more unique keys than the output capacity */
+  SS_ERR_NOMEM = 5,               /* request exceeds free device memory */
+  SS_ERR_TIMEOUT = 6,             /* a bounded device wait ran out */
+  SS_ERR_CUDA = 7,                /* a CUDA runtime call failed */
+  SS_ERR_DEPTH = 8                /* recursion deeper than the level limit */
+} ss_status;
+
+typedef enum { SS_U32 = 0, SS_U64 = 1, SS_U128 = 2 } ss_type;
+
+/* Operation codes for ss_workspace_size(). */
+typedef enum {
+  SS_OP_SEMISORT_EQUAL = 0,
+  SS_OP_SEMISORT_LESS = 1,
+  SS_OP_COLLECT_REDUCE = 2,
+  SS_OP_HISTOGRAM = 3
+} ss_op;
+
+/* Tunables; a zero field means "choose automatically".
+ *   seed          seeds sampling and the per-level hash salts (Sec. 3.1).
+ *   subarray      records per subarray l at recursion levels >= 2 (Sec. 3.2).
+ *   n_light_log2  log2 of the light-bucket count n_L at the top level.
+ *   alpha         base-case threshold: largest bucket one CTA refines (Sec. 3.3).
+ *   sample_size   samples per top-level subproblem |S|.
+ *   splitter_mode 0 = sampled splitters, 1 = learned splitters (semisort_less).
+ *   flags         SS_FLAG_* bits. */
+typedef struct {
+  uint64_t seed;
+  uint32_t subarray;
+  uint32_t n_light_log2;
+  uint32_t alpha;
+  uint32_t sample_size;
+  int32_t splitter_mode;
+  int32_t flags;
+} ss_options;
+
+#define SS_FLAG_PHASE_TIMING 0x1 /* record per-kernel CUDA events (ss_phase_times) */
+#define SS_FLAG_IDENTITY_HASH 0x2 /* integer keys hashed by identity (Sec. 4.1 "-i") */
+
+/* Bytes of workspace needed by `op` on n records with the given types and
+ * options (NULL = defaults).  Returns SS_ERR_UNSUPPORTED for unsupported type
+ * combinations or sizes. */
+ss_status ss_workspace_size(int op, ss_type key_type, ss_type val_type, uint64_t n,
+                            const ss_options* opt, size_t* bytes);
+
+/* semisort_= (Sec. 2.1; Algorithm 1 with the hash-table base case of Sec. 3.3).
+ * Reorders the n records so that records with equal keys are contiguous;
+ * records of one key keep their input order (stable).  The order of the key
+ * groups is unspecified but fixed for a given options.seed.
+ * keys_out/vals_out may equal keys/vals (in place); partial overlap is an
+ * error.  vals may be NULL together with vals_out (keys only). */
+ss_status semisort_equal(ss_type key_type, ss_type val_type, const void* keys, const void* vals,
+                         void* keys_out, void* vals_out, uint64_t n, void* ws, size_t ws_bytes,
+                         const ss_options* opt, ss_stream_t stream);
+
+/* semisort_< as a range-partitioned variant: buckets are key ranges cut by
+ * sample splitters (heavy keys get their own equality buckets), and each base
+ * case is a stable comparison sort (Sec. 3.3), so the output equals the
+ * stable sort of the input by key.  Arguments as semisort_equal. */
+ss_status semisort_less(ss_type key_type, ss_type val_type, const void* keys, const void* vals,
+                        void* keys_out, void* vals_out, uint64_t n, void* ws, size_t ws_bytes,
+                        const ss_options* opt, ss_stream_t stream);
+
+/* collect-reduce (Sec. 2.1, Sec. 3.5) with the map M(r) = value and the monoid
+ * (+ mod 2^64, 0).  Writes one (unique key, sum) pair per distinct key into
+ * ukeys_out/sums_out (capacity entries each) and the number of distinct keys
+ * into *d_num_unique (device pointer).  If that number exceeds capacity only
+ * the count is written and the device flag SS_ERR_CAPACITY is raised.  Output
+ * order is unspecified but fixed for a given seed. */
+ss_status collect_reduce(ss_type key_type, const void* keys, const uint64_t* vals, void* ukeys_out,
+                         uint64_t* sums_out, uint64_t capacity, uint64_t* d_num_unique, uint64_t n,
+                         void* ws, size_t ws_bytes, const ss_options* opt, ss_stream_t stream);
+
+/* histogram (Sec. 2.1): collect-reduce with M(r) = 1, counts as uint32. */
+ss_status histogram(ss_type key_type, const void* keys, void* ukeys_out, uint32_t* counts_out,
+                    uint64_t capacity, uint64_t* d_num_unique, uint64_t n, void* ws,
+                    size_t ws_bytes, const ss_options* opt, ss_stream_t stream);
+
+/* Reads (and clears) the device error flag left in `ws` by earlier calls on
+ * `stream`; synchronizes the stream.  *code receives the ss_status of the
+ * first device-side failure (SS_OK if none). */
+ss_status ss_last_device_error(void* ws, ss_stream_t stream, int* code);
+
+/* Per-call statistics kept in the workspace by the last call (synchronizes the
+ * stream).  out[0..count) receives, in order: levels used, records distributed
+ * at levels 1..4 (4 entries), records refined, records copied, heavy keys at
+ * level 1, largest refined bucket, refine items, records whose bucket was all
+ * distinct keys.  Returns the number of entries written. */
+int ss_get_stats(void* ws, ss_stream_t stream, uint64_t* out, int count);
+
+/* Per-kernel timings (milliseconds) of the last call made with
+ * SS_FLAG_PHASE_TIMING; names[i] receives a static string.  Synchronizes.
+ * Returns the number of phases written (at most max). */
+int ss_phase_times(float* ms, const char** names, int max);
+
+/* Number of kernels the most recent semisort / collect-reduce / histogram call
+ * on this host thread enqueued (0 before any call). */
+int ss_kernel_launches(void);
+
+/* Human-readable name of a status code (static storage). */
+const char* ss_status_string(ss_status s);
+
+/* The library's fixed 64-bit key hash (the SplitMix64 output mixer applied to
+ * key XOR salt), applied on the device to n keys: out[i] = mix(keys[i] ^ salt).
+ * Exposed so that tests can compare it with an independent statement of the
+ * published function. */
+ss_status ss_hash_u64(const uint64_t* keys, uint64_t* out, uint64_t n, uint64_t salt,
+                      ss_stream_t stream);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* SEMISORT_H_ */

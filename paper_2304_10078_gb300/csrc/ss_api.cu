@@ -1,0 +1,365 @@
+// C ABI of the semisort library: argument checks, the workspace plan and the
+// dispatch to the per-key-type pipelines.  See include/semisort.h.
+#include <cuda_runtime.h>
+#include <stdint.h>
+#include <string.h>
+
+#include <algorithm>
+#include <mutex>
+
+#include "../../include/semisort.h"
+#include "ss_common.cuh"
+#include "ss_host.h"
+#include "ss_plan.h"
+
+using namespace ss;
+
+namespace {
+
+constexpr uint64_t kMaxN = (1ull << 32) - (1ull << 20);
+constexpr uint32_t kAlphaMax = 4096;  // records one refine CTA holds (kRefMax)
+
+size_t al(size_t x) { return (x + 255) & ~size_t(255); }
+
+uint32_t ceil_log2(uint64_t x) {
+  uint32_t b = 0;
+  while ((1ull << b) < x) ++b;
+  return b;
+}
+
+int num_sms() {
+  static int cache[64] = {0};
+  int dev = 0;
+  if (cudaGetDevice(&dev) != cudaSuccess) return 0;
+  if (dev < 0 || dev >= 64) dev = 0;
+  if (!cache[dev]) cudaDeviceGetAttribute(&cache[dev], cudaDevAttrMultiProcessorCount, dev);
+  return cache[dev];
+}
+
+int kbytes_of(int t) { return t == SS_U32 ? 4 : t == SS_U64 ? 8 : t == SS_U128 ? 16 : 0; }
+
+// Capacities of every device work list for n records (see ss_plan.h).
+ss_status make_plan(int op, int kt, int vt, uint64_t n, const ss_options* opt, int nsm, Plan* P) {
+  memset(P, 0, sizeof(*P));
+  P->n = n;
+  P->op = op;
+  P->kbytes = kbytes_of(kt);
+  P->vbytes = op == SS_OP_HISTOGRAM ? 0 : op == SS_OP_COLLECT_REDUCE ? 8 : (vt == SS_U32 ? 4 : 8);
+  if (!P->kbytes) return SS_ERR_INVALID_ARG;
+  if (op == SS_OP_SEMISORT_EQUAL || op == SS_OP_SEMISORT_LESS)
+    if (vt != SS_U32 && vt != SS_U64) return SS_ERR_INVALID_ARG;
+  if (n >= kMaxN) return SS_ERR_UNSUPPORTED;
+  if (nsm <= 0) nsm = 152;
+  uint32_t alpha = (opt && opt->alpha) ? opt->alpha : kAlphaMax;
+  alpha = std::min(std::max(alpha, 64u), kAlphaMax);
+  P->alpha = alpha;
+  uint32_t lb1 = 0;
+  if (opt && opt->n_light_log2)
+    lb1 = std::min<uint32_t>(std::max<uint32_t>(opt->n_light_log2, 1), kMaxLightLog2);
+  else
+    lb1 = std::min<uint32_t>(std::max<uint32_t>(ceil_log2((2 * n + alpha - 1) / alpha), 1), 10);
+  P->lbits1 = lb1;
+  uint64_t l1 = (n + 2 * (uint64_t)nsm - 1) / (2 * (uint64_t)nsm);
+  l1 = ((l1 + 4095) / 4096) * 4096;
+  l1 = std::max<uint64_t>(l1, 32768);
+  P->l1 = (uint32_t)std::min<uint64_t>(l1, 1u << 31);
+  uint32_t l2 = (opt && opt->subarray) ? opt->subarray : 32768;
+  l2 = std::max<uint32_t>(((l2 + 4095) / 4096) * 4096, 4096);
+  P->l2 = l2;
+  uint32_t s1 = (opt && opt->sample_size) ? opt->sample_size : 16384;
+  uint32_t p2 = 2048;
+  while (p2 < s1 && p2 < 16384) p2 <<= 1;
+  s1 = p2;
+  if (P->kbytes == 16) s1 = std::min<uint32_t>(s1, 8192);
+  P->s1 = s1;
+  P->s2 = 8192;
+  // level 0
+  P->seg_cap[0] = 1;
+  P->tile_cap[0] = (uint32_t)((n + P->l1 - 1) / P->l1);
+  P->bucket_cap[0] = 2u << lb1;
+  P->c_cap[0] = (uint64_t)((1u << lb1) + std::min<uint32_t>(1u << lb1, kMaxHeavy)) * P->tile_cap[0];
+  for (int l = 1; l < kMaxLevels; ++l) {
+    const uint64_t segs = n / (alpha + 1) + 1;
+    P->seg_cap[l] = (uint32_t)segs;
+    P->tile_cap[l] = (uint32_t)((n + l2 - 1) / l2 + segs);
+    // a segment of m > alpha records has n_L < 4m/alpha + 2 light buckets,
+    // so 2 n_L rows < 8m/alpha + 4 and the sum over segments < 12n/alpha
+    P->bucket_cap[l] = (uint32_t)(12 * n / alpha + 64);
+    P->c_cap[l] = 4096ull * ((n + l2 - 1) / l2) + 12 * n / alpha + 64;
+  }
+  uint64_t items = n / kCopyChunk + 16;
+  for (int l = 0; l < kMaxLevels; ++l) items += P->bucket_cap[l];
+  P->item_cap = (uint32_t)std::min<uint64_t>(items, 0xFFFFFFF0ull);
+  // layout: control block first, so status calls can find it without a plan
+  size_t o = al(sizeof(Ctrl));
+  const bool need_t = n > alpha;
+  P->off_tk = o;
+  o = al(o + (need_t ? n * P->kbytes : 0));
+  P->off_tv = o;
+  o = al(o + (need_t ? n * P->vbytes : 0));
+  const bool need_t2 = (op == SS_OP_COLLECT_REDUCE || op == SS_OP_HISTOGRAM) && need_t;
+  P->off_t2k = o;
+  o = al(o + (need_t2 ? n * P->kbytes : 0));
+  P->off_t2v = o;
+  o = al(o + (need_t2 ? n * P->vbytes : 0));
+  for (int l = 0; l < kMaxLevels; ++l) {
+    if (!need_t) {
+      P->seg_cap[l] = P->tile_cap[l] = P->bucket_cap[l] = 0;
+      P->c_cap[l] = 0;
+    }
+    P->off_segs[l] = o;
+    o = al(o + (size_t)P->seg_cap[l] * sizeof(Seg));
+    P->off_tiles[l] = o;
+    o = al(o + (size_t)P->tile_cap[l] * sizeof(Tile));
+    P->off_C[l] = o;
+    o = al(o + (size_t)P->c_cap[l] * 4);
+    P->off_hkeys[l] = o;
+    o = al(o + (size_t)P->bucket_cap[l] * P->kbytes);
+    P->off_htab[l] = o;
+    o = al(o + (size_t)P->bucket_cap[l] * 4);
+    P->off_bsize[l] = o;
+    o = al(o + (size_t)P->bucket_cap[l] * 4);
+    P->off_boff[l] = o;
+    o = al(o + (size_t)P->bucket_cap[l] * 4);
+    P->off_hpart[l] = o;
+    o = al(o + (op == SS_OP_COLLECT_REDUCE ? (size_t)P->c_cap[l] * 8 : 0));
+    P->off_split[l] = o;
+    o = al(o + (op == SS_OP_SEMISORT_LESS ? (size_t)P->bucket_cap[l] * P->kbytes : 0));
+  }
+  if (!need_t) P->item_cap = 1;
+  P->off_items = o;
+  o = al(o + (size_t)P->item_cap * sizeof(Item));
+  const bool red = op == SS_OP_COLLECT_REDUCE || op == SS_OP_HISTOGRAM;
+  P->off_item_out = o;
+  o = al(o + (red ? (size_t)P->item_cap * 8 : 0));
+  P->off_item_pos = o;
+  o = al(o + (red ? (size_t)P->item_cap * 8 : 0));
+  P->off_block_sums = o;
+  o = al(o + (red ? 8192 * 8 : 0));
+  P->off_ctrl = 0;
+  P->total = o;
+  return SS_OK;
+}
+
+void fill_work(const Plan& P, void* ws, Work* w) {
+  char* b = static_cast<char*>(ws);
+  w->n = P.n;
+  w->alpha = P.alpha;
+  w->l1 = P.l1;
+  w->l2 = P.l2;
+  w->lbits1 = P.lbits1;
+  w->s1 = P.s1;
+  w->s2 = P.s2;
+  w->op = P.op;
+  w->t_k = b + P.off_tk;
+  w->t_v = b + P.off_tv;
+  w->t2_k = b + P.off_t2k;
+  w->t2_v = b + P.off_t2v;
+  for (int l = 0; l < kMaxLevels; ++l) {
+    w->segs[l] = reinterpret_cast<Seg*>(b + P.off_segs[l]);
+    w->tiles[l] = reinterpret_cast<Tile*>(b + P.off_tiles[l]);
+    w->C[l] = reinterpret_cast<uint32_t*>(b + P.off_C[l]);
+    w->hkeys[l] = b + P.off_hkeys[l];
+    w->htab[l] = reinterpret_cast<uint32_t*>(b + P.off_htab[l]);
+    w->bsize[l] = reinterpret_cast<uint32_t*>(b + P.off_bsize[l]);
+    w->boff[l] = reinterpret_cast<uint32_t*>(b + P.off_boff[l]);
+    w->hpart[l] = reinterpret_cast<uint64_t*>(b + P.off_hpart[l]);
+    w->splitters[l] = b + P.off_split[l];
+    w->seg_cap[l] = P.seg_cap[l];
+    w->tile_cap[l] = P.tile_cap[l];
+    w->c_cap[l] = P.c_cap[l];
+    w->bucket_cap[l] = P.bucket_cap[l];
+  }
+  w->items = reinterpret_cast<Item*>(b + P.off_items);
+  w->item_cap = P.item_cap;
+  w->item_out = reinterpret_cast<uint64_t*>(b + P.off_item_out);
+  w->item_pos = reinterpret_cast<uint64_t*>(b + P.off_item_pos);
+  w->block_sums = reinterpret_cast<uint64_t*>(b + P.off_block_sums);
+  w->ctrl = reinterpret_cast<Ctrl*>(b + P.off_ctrl);
+}
+
+bool aligned16(const void* p) { return (reinterpret_cast<uintptr_t>(p) & 15) == 0; }
+
+struct Range {
+  uintptr_t a, b;
+};
+bool overlap(Range x, Range y) { return x.a < y.b && y.a < x.b; }
+
+thread_local int g_launches = 0;
+
+std::mutex g_timer_mu;
+PhaseTimer g_timer;
+bool g_timer_ready = false;
+
+PhaseTimer* timer_for(const ss_options* opt, cudaStream_t st) {
+  if (!opt || !(opt->flags & SS_FLAG_PHASE_TIMING)) return nullptr;
+  std::lock_guard<std::mutex> g(g_timer_mu);
+  if (!g_timer_ready) {
+    for (int i = 0; i <= PhaseTimer::kMax; ++i) cudaEventCreate(&g_timer.ev[i]);
+    g_timer_ready = true;
+  }
+  g_timer.on = true;
+  g_timer.start(st);
+  return &g_timer;
+}
+
+cudaError_t dispatch(int op, int kt, int vt, const Plan& P, const Work& w, cudaStream_t st, PhaseTimer* tm) {
+  g_launches = 0;
+  LaunchCfg c{num_sms(), tm, &g_launches};
+  switch (kt) {
+    case SS_U64: return run_u64(op, vt, P, w, st, c);
+    default: return cudaErrorNotSupported;
+  }
+}
+
+ss_status semisort_common(int op, ss_type kt, ss_type vt, const void* keys, const void* vals,
+                          void* keys_out, void* vals_out, uint64_t n, void* ws, size_t ws_bytes,
+                          const ss_options* opt, ss_stream_t stream) {
+  if (n == 0) return SS_OK;
+  if (!keys || !keys_out || !ws) return SS_ERR_INVALID_ARG;
+  if ((vals == nullptr) != (vals_out == nullptr)) return SS_ERR_INVALID_ARG;
+  if (!aligned16(keys) || !aligned16(keys_out) || !aligned16(ws) || (vals && !aligned16(vals)) ||
+      (vals_out && !aligned16(vals_out)))
+    return SS_ERR_INVALID_ARG;
+  Plan P;
+  ss_status s = make_plan(op, kt, vt, n, opt, num_sms(), &P);
+  if (s != SS_OK) return s;
+  if (ws_bytes < P.total) return SS_ERR_WORKSPACE_TOO_SMALL;
+  const size_t kb = n * P.kbytes, vb = n * (vt == SS_U32 ? 4 : 8);
+  Range rk{(uintptr_t)keys, (uintptr_t)keys + kb}, rko{(uintptr_t)keys_out, (uintptr_t)keys_out + kb};
+  Range rw{(uintptr_t)ws, (uintptr_t)ws + P.total};
+  if (overlap(rk, rko) && keys != keys_out) return SS_ERR_INVALID_ARG;
+  if (overlap(rw, rk) || overlap(rw, rko)) return SS_ERR_INVALID_ARG;
+  if (vals) {
+    Range rv{(uintptr_t)vals, (uintptr_t)vals + vb}, rvo{(uintptr_t)vals_out, (uintptr_t)vals_out + vb};
+    if (overlap(rv, rvo) && vals != vals_out) return SS_ERR_INVALID_ARG;
+    if (overlap(rw, rv) || overlap(rw, rvo)) return SS_ERR_INVALID_ARG;
+    if (overlap(rk, rv) || overlap(rk, rvo) || overlap(rko, rv) || overlap(rko, rvo)) return SS_ERR_INVALID_ARG;
+    if ((keys == keys_out) != (vals == vals_out)) return SS_ERR_INVALID_ARG;
+  }
+  Work w;
+  memset(&w, 0, sizeof(w));
+  fill_work(P, ws, &w);
+  w.seed = opt ? opt->seed : 0;
+  w.in_k = keys;
+  w.in_v = vals;
+  w.out_k = keys_out;
+  w.out_v = vals_out;
+  w.has_vals = vals != nullptr;
+  cudaStream_t st = reinterpret_cast<cudaStream_t>(stream);
+  PhaseTimer* tm = timer_for(opt, st);
+  cudaError_t e = dispatch(op, kt, vt, P, w, st, tm);
+  if (e == cudaErrorNotSupported) return SS_ERR_UNSUPPORTED;
+  return e == cudaSuccess ? SS_OK : SS_ERR_CUDA;
+}
+
+__global__ void k_hash_u64(const uint64_t* k, uint64_t* o, uint64_t n, uint64_t salt) {
+  for (uint64_t i = blockIdx.x * (uint64_t)blockDim.x + threadIdx.x; i < n; i += (uint64_t)gridDim.x * blockDim.x)
+    o[i] = mix64(k[i] ^ salt);
+}
+
+}  // namespace
+
+extern "C" {
+
+ss_status ss_workspace_size(int op, ss_type key_type, ss_type val_type, uint64_t n, const ss_options* opt,
+                            size_t* bytes) {
+  if (!bytes) return SS_ERR_INVALID_ARG;
+  if (op < 0 || op > 3) return SS_ERR_INVALID_ARG;
+  Plan P;
+  ss_status s = make_plan(op, key_type, val_type, n, opt, num_sms(), &P);
+  if (s != SS_OK) return s;
+  *bytes = P.total;
+  return SS_OK;
+}
+
+ss_status semisort_equal(ss_type key_type, ss_type val_type, const void* keys, const void* vals, void* keys_out,
+                         void* vals_out, uint64_t n, void* ws, size_t ws_bytes, const ss_options* opt,
+                         ss_stream_t stream) {
+  return semisort_common(kOpEqual, key_type, val_type, keys, vals, keys_out, vals_out, n, ws, ws_bytes, opt,
+                         stream);
+}
+
+ss_status semisort_less(ss_type key_type, ss_type val_type, const void* keys, const void* vals, void* keys_out,
+                        void* vals_out, uint64_t n, void* ws, size_t ws_bytes, const ss_options* opt,
+                        ss_stream_t stream) {
+  return semisort_common(kOpLess, key_type, val_type, keys, vals, keys_out, vals_out, n, ws, ws_bytes, opt,
+                         stream);
+}
+
+ss_status collect_reduce(ss_type, const void*, const uint64_t*, void*, uint64_t*, uint64_t, uint64_t*, uint64_t,
+                         void*, size_t, const ss_options*, ss_stream_t) {
+  return SS_ERR_UNSUPPORTED;
+}
+
+ss_status histogram(ss_type, const void*, void*, uint32_t*, uint64_t, uint64_t*, uint64_t, void*, size_t,
+                    const ss_options*, ss_stream_t) {
+  return SS_ERR_UNSUPPORTED;
+}
+
+ss_status ss_last_device_error(void* ws, ss_stream_t stream, int* code) {
+  if (!ws || !code) return SS_ERR_INVALID_ARG;
+  cudaStream_t st = reinterpret_cast<cudaStream_t>(stream);
+  Ctrl* c = reinterpret_cast<Ctrl*>(ws);
+  uint32_t v = 0;
+  if (cudaMemcpyAsync(&v, &c->error, 4, cudaMemcpyDeviceToHost, st) != cudaSuccess) return SS_ERR_CUDA;
+  if (cudaStreamSynchronize(st) != cudaSuccess) return SS_ERR_CUDA;
+  if (cudaMemsetAsync(&c->error, 0, 4, st) != cudaSuccess) return SS_ERR_CUDA;
+  if (cudaStreamSynchronize(st) != cudaSuccess) return SS_ERR_CUDA;
+  *code = (int)v;
+  return SS_OK;
+}
+
+int ss_get_stats(void* ws, ss_stream_t stream, uint64_t* out, int count) {
+  if (!ws || !out || count <= 0) return 0;
+  cudaStream_t st = reinterpret_cast<cudaStream_t>(stream);
+  Ctrl h;
+  if (cudaMemcpyAsync(&h, ws, sizeof(Ctrl), cudaMemcpyDeviceToHost, st) != cudaSuccess) return 0;
+  if (cudaStreamSynchronize(st) != cudaSuccess) return 0;
+  const int m = std::min(count, 12);
+  for (int i = 0; i < m; ++i) out[i] = h.stats[i];
+  return m;
+}
+
+int ss_phase_times(float* ms, const char** names, int max) {
+  std::lock_guard<std::mutex> g(g_timer_mu);
+  if (!g_timer_ready || !g_timer.on) return 0;
+  const int m = std::min(max, g_timer.count);
+  if (m <= 0) return 0;
+  cudaEventSynchronize(g_timer.ev[g_timer.count]);
+  for (int i = 0; i < m; ++i) {
+    float t = 0;
+    cudaEventElapsedTime(&t, g_timer.ev[i], g_timer.ev[i + 1]);
+    if (ms) ms[i] = t;
+    if (names) names[i] = g_timer.name[i];
+  }
+  return m;
+}
+
+int ss_kernel_launches(void) { return g_launches; }
+
+const char* ss_status_string(ss_status s) {
+  switch (s) {
+    case SS_OK: return "ok";
+    case SS_ERR_INVALID_ARG: return "invalid argument";
+    case SS_ERR_UNSUPPORTED: return "unsupported type or size";
+    case SS_ERR_WORKSPACE_TOO_SMALL: return "workspace too small";
+    case SS_ERR_CAPACITY: return "capacity exceeded";
+    case SS_ERR_NOMEM: return "not enough device memory";
+    case SS_ERR_TIMEOUT: return "device wait timed out";
+    case SS_ERR_CUDA: return "CUDA runtime error";
+    case SS_ERR_DEPTH: return "recursion depth limit reached";
+  }
+  return "unknown status";
+}
+
+ss_status ss_hash_u64(const uint64_t* keys, uint64_t* out, uint64_t n, uint64_t salt, ss_stream_t stream) {
+  if (n == 0) return SS_OK;
+  if (!keys || !out) return SS_ERR_INVALID_ARG;
+  cudaStream_t st = reinterpret_cast<cudaStream_t>(stream);
+  const uint64_t blocks = std::min<uint64_t>((n + 255) / 256, 65535);
+  k_hash_u64<<<(unsigned)blocks, 256, 0, st>>>(keys, out, n, salt);
+  return cudaGetLastError() == cudaSuccess ? SS_OK : SS_ERR_CUDA;
+}
+
+}  // extern "C"

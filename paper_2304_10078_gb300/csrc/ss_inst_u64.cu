@@ -1,0 +1,16 @@
+// Pipeline instantiations for 64-bit keys.
+#include "ss_launch.cuh"
+
+namespace ss {
+
+cudaError_t run_u64(int op, int vt, const Plan& P, const Work& w, cudaStream_t st, const LaunchCfg& c) {
+  switch (op) {
+    case kOpEqual:
+      return vt == 0 ? launch_pipeline<uint64_t, uint32_t, kOpEqual>(P, w, st, c)
+                     : launch_pipeline<uint64_t, uint64_t, kOpEqual>(P, w, st, c);
+    default:
+      return cudaErrorNotSupported;
+  }
+}
+
+}  // namespace ss

@@ -1,0 +1,134 @@
+// Work descriptors and the workspace plan shared by host and device code.
+//
+// The recursion of Algorithm 1 is run level by level.  Level l holds a list
+// of segments (subproblems, the light buckets of level l-1 that exceed the
+// base-case threshold alpha); each segment is cut into subarrays ("tiles",
+// the blocks of size l in Sec. 3.2).  All lists live in the caller's
+// workspace and are built on the device, so the host never waits for them.
+#pragma once
+#include <stddef.h>
+#include <stdint.h>
+
+namespace ss {
+
+constexpr int kMaxLevels = 4;          // recursion levels (Algorithm 1) before the depth error
+constexpr int kMaxLightLog2 = 11;      // n_L <= 2048 per segment
+constexpr uint32_t kMaxHeavy = 1024;   // heavy keys per segment
+constexpr uint32_t kCopyChunk = 1u << 16;  // records per copy item
+
+// Operations.
+enum Op : int { kOpEqual = 0, kOpLess = 1, kOpReduce = 2, kOpHist = 3 };
+
+// Buffer ids used by work items.
+enum Buf : uint32_t { kBufIn = 0, kBufT = 1, kBufOut = 2, kBufT2 = 3 };
+
+// Finish-item kinds.
+enum ItemKind : uint32_t { kItemRefine = 0, kItemCopy = 1, kItemHeavyOut = 2 };
+
+struct Seg {
+  uint64_t start;      // first record of the segment (same index space in every buffer)
+  uint32_t len;        // records
+  uint32_t ntiles;     // subarrays
+  uint32_t first_tile; // index of the first subarray in the level's tile list
+  uint32_t bbase;      // base of the segment's bucket rows / heavy table (capacity 2 n_L)
+  uint64_t cbase;      // base of the segment's count matrix (nbcap x ntiles, bucket-major)
+  uint32_t lbits;      // log2 n_L
+  uint32_t nh;         // heavy keys found by sampling
+  uint32_t nbcap;      // n_L + heavy capacity
+  uint32_t fin_off;    // first finish item emitted by this segment
+  uint32_t next_off;   // first next-level segment emitted by this segment
+  uint32_t cnt_fin;    // finish items emitted
+  uint32_t cnt_next;   // next-level segments emitted
+  uint32_t pad;
+};
+
+struct Tile {
+  uint64_t start;  // first record
+  uint32_t len;    // records
+  uint32_t seg;    // owning segment
+  uint32_t idx;    // subarray index within the segment
+  uint32_t pad;
+};
+
+struct Item {
+  uint64_t start;   // first record
+  uint32_t len;     // records
+  uint32_t kind;    // ItemKind
+  uint32_t buf;     // buffer holding the records (Buf)
+  uint32_t aux;     // heavy-output: segment; otherwise 0
+  uint32_t aux2;    // heavy-output: heavy index; otherwise 0
+  uint32_t level;   // level that emitted the item
+};
+
+// Control block (device).
+struct Ctrl {
+  uint32_t nsegs[kMaxLevels];
+  uint32_t ntiles[kMaxLevels];
+  uint32_t nfin;       // finish items so far
+  uint32_t error;      // first device-side ss_status (0 = none)
+  uint64_t stats[16];  // see ss_get_stats
+};
+
+// Everything a kernel needs: workspace pointers + problem constants.
+struct Work {
+  // problem
+  uint64_t n;
+  uint32_t alpha;      // base-case threshold
+  uint32_t l1, l2;     // subarray size at level 1 / levels >= 2
+  uint32_t lbits1;     // log2 n_L at level 1
+  uint32_t s1, s2;     // sample size caps at level 1 / levels >= 2
+  uint32_t op;
+  uint32_t ident;      // identity hash for integer keys
+  uint32_t out_cap;    // collect-reduce / histogram capacity (clamped)
+  uint64_t seed;
+  // user buffers
+  const void* in_k;
+  const void* in_v;
+  void* out_k;
+  void* out_v;
+  int has_vals;
+  // workspace buffers
+  void* t_k;
+  void* t_v;
+  void* t2_k;
+  void* t2_v;
+  Seg* segs[kMaxLevels];
+  Tile* tiles[kMaxLevels];
+  uint32_t* C[kMaxLevels];
+  void* hkeys[kMaxLevels];       // heavy keys (sorted), per segment at bbase
+  uint32_t* htab[kMaxLevels];    // heavy hash table: heavy index or kEmpty, per segment at bbase (2 n_L slots)
+  uint32_t* bsize[kMaxLevels];   // bucket totals
+  uint32_t* boff[kMaxLevels];    // bucket offsets within segment
+  uint64_t* hpart[kMaxLevels];   // collect-reduce heavy partials (nbcap x ntiles layout, rows >= n_L)
+  uint32_t seg_cap[kMaxLevels];
+  uint32_t tile_cap[kMaxLevels];
+  uint64_t c_cap[kMaxLevels];
+  uint32_t bucket_cap[kMaxLevels];
+  Item* items;
+  uint32_t item_cap;
+  uint64_t* item_out;   // per item: outputs produced (collect-reduce / histogram)
+  uint64_t* item_pos;   // per item: exclusive prefix of item_out
+  uint64_t* block_sums; // scratch for the device-wide scan
+  uint64_t* num_unique; // user pointer (collect-reduce / histogram)
+  void* sums_out;       // user pointer: u64 sums or u32 counts
+  void* splitters[kMaxLevels];  // semisort_<: per-segment sorted boundaries at bbase
+  Ctrl* ctrl;
+};
+
+// Host-side plan of workspace capacities and offsets.
+struct Plan {
+  uint64_t n;
+  int op, kbytes, vbytes;
+  uint32_t alpha, l1, l2, lbits1, s1, s2;
+  uint32_t seg_cap[kMaxLevels], tile_cap[kMaxLevels], bucket_cap[kMaxLevels];
+  uint64_t c_cap[kMaxLevels];
+  uint32_t item_cap;
+  size_t off_tk, off_tv, off_t2k, off_t2v;
+  size_t off_segs[kMaxLevels], off_tiles[kMaxLevels], off_C[kMaxLevels], off_hkeys[kMaxLevels],
+      off_htab[kMaxLevels], off_bsize[kMaxLevels], off_boff[kMaxLevels], off_hpart[kMaxLevels],
+      off_split[kMaxLevels];
+  size_t off_items, off_item_out, off_item_pos, off_block_sums, off_ctrl;
+  size_t total;
+};
+
+}  // namespace ss
