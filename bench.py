@@ -166,6 +166,7 @@ def main():
     ap.add_argument("--cpu-sample", type=int, default=1 << 24)
     ap.add_argument("--e2e-steps", type=int, default=3)
     ap.add_argument("--quick", action="store_true", help="small smoke configuration (not a bench number)")
+    ap.add_argument("--dists", default="", help="comma-separated indices into the distribution list")
     args = ap.parse_args()
 
     rank = int(os.environ.get("RANK", "0"))
@@ -186,7 +187,7 @@ def main():
         dist.init_process_group("nccl", device_id=torch.device("cuda", local))
     ss.lib()
     n = args.n
-    dists = DISTS
+    dists = [DISTS[int(i)] for i in args.dists.split(",")] if args.dists else DISTS
     # device-resident inputs: one key array per distribution, one value array
     keys = []
     vals = sg.iota(n)
@@ -208,6 +209,7 @@ def main():
     assert ss.last_device_error(ws) == 0
 
     per_dist = {dist_name(d): [] for d in dists}
+    phases = {}
     dominant, dom_bytes, alg_total = [], [], 0
     launches = 0
     clocks = Clocks(local)
@@ -229,6 +231,8 @@ def main():
         ph = dict()
         for name, ms in ss.phase_times():
             ph[name] = ph.get(name, 0.0) + ms
+        for name, ms in ph.items():
+            phases.setdefault(name, []).append(ms)
         st = ss.stats(ws)
         alg_total += alg_bytes(st)
         dominant.append(ph.get("distribute.L0", float("nan")))
@@ -309,6 +313,7 @@ def main():
                           "achieved_gbs": alg_total / (elapsed_ms / 1000.0) / 1e9,
                           "frac": alg_total / (elapsed_ms / 1000.0) / 1e9 / peak},
         "per_distribution_ms": {k: (sum(v) / len(v) if v else None) for k, v in per_dist.items()},
+        "phase_ms": {k: sum(v) / len(v) for k, v in phases.items()},
         "cpu_baseline": cpu,
         "e2e": e2e,
         "gpu_launches": launches,

@@ -57,7 +57,7 @@ ss_status make_plan(int op, int kt, int vt, uint64_t n, const ss_options* opt, i
   if (opt && opt->n_light_log2)
     lb1 = std::min<uint32_t>(std::max<uint32_t>(opt->n_light_log2, 1), kMaxLightLog2);
   else
-    lb1 = std::min<uint32_t>(std::max<uint32_t>(ceil_log2((2 * n + alpha - 1) / alpha), 1), 10);
+    lb1 = std::min<uint32_t>(std::max<uint32_t>(ceil_log2((2 * n + alpha - 1) / alpha), 1), kMaxLightLog2);
   P->lbits1 = lb1;
   uint64_t l1 = (n + 2 * (uint64_t)nsm - 1) / (2 * (uint64_t)nsm);
   l1 = ((l1 + 4095) / 4096) * 4096;
@@ -85,23 +85,23 @@ ss_status make_plan(int op, int kt, int vt, uint64_t n, const ss_options* opt, i
     // a segment of m > alpha records has n_L < 4m/alpha + 2 light buckets,
     // so 2 n_L rows < 8m/alpha + 4 and the sum over segments < 12n/alpha
     P->bucket_cap[l] = (uint32_t)(12 * n / alpha + 64);
-    P->c_cap[l] = 4096ull * ((n + l2 - 1) / l2) + 12 * n / alpha + 64;
+    P->c_cap[l] = (uint64_t)kMaxBuckets * ((n + l2 - 1) / l2) + 12 * n / alpha + 64;
   }
   uint64_t items = n / kCopyChunk + 16;
   for (int l = 0; l < kMaxLevels; ++l) items += P->bucket_cap[l];
   P->item_cap = (uint32_t)std::min<uint64_t>(items, 0xFFFFFFF0ull);
   // layout: control block first, so status calls can find it without a plan
   size_t o = al(sizeof(Ctrl));
+  // temporaries T and T2 hold records (key, value) as array of structures
   const bool need_t = n > alpha;
+  const size_t ralign = std::max(P->kbytes == 16 ? 16 : P->kbytes, P->vbytes);
+  const size_t recbytes = (P->kbytes + P->vbytes + ralign - 1) / ralign * ralign;
   P->off_tk = o;
-  o = al(o + (need_t ? n * P->kbytes : 0));
+  o = al(o + (need_t ? n * recbytes : 0));
   P->off_tv = o;
-  o = al(o + (need_t ? n * P->vbytes : 0));
-  const bool need_t2 = (op == SS_OP_COLLECT_REDUCE || op == SS_OP_HISTOGRAM) && need_t;
   P->off_t2k = o;
-  o = al(o + (need_t2 ? n * P->kbytes : 0));
+  o = al(o + (need_t ? n * recbytes : 0));
   P->off_t2v = o;
-  o = al(o + (need_t2 ? n * P->vbytes : 0));
   for (int l = 0; l < kMaxLevels; ++l) {
     if (!need_t) {
       P->seg_cap[l] = P->tile_cap[l] = P->bucket_cap[l] = 0;
@@ -160,7 +160,7 @@ void fill_work(const Plan& P, void* ws, Work* w) {
     w->tiles[l] = reinterpret_cast<Tile*>(b + P.off_tiles[l]);
     w->C[l] = reinterpret_cast<uint32_t*>(b + P.off_C[l]);
     w->hkeys[l] = b + P.off_hkeys[l];
-    w->htab[l] = reinterpret_cast<uint32_t*>(b + P.off_htab[l]);
+    w->htab[l] = reinterpret_cast<uint16_t*>(b + P.off_htab[l]);
     w->bsize[l] = reinterpret_cast<uint32_t*>(b + P.off_bsize[l]);
     w->boff[l] = reinterpret_cast<uint32_t*>(b + P.off_boff[l]);
     w->hpart[l] = reinterpret_cast<uint64_t*>(b + P.off_hpart[l]);
@@ -203,6 +203,7 @@ PhaseTimer* timer_for(const ss_options* opt, cudaStream_t st) {
   return &g_timer;
 }
 
+// vt: 0 = u32 values, 1 = u64 values, 2 = keys only.
 cudaError_t dispatch(int op, int kt, int vt, const Plan& P, const Work& w, cudaStream_t st, PhaseTimer* tm) {
   g_launches = 0;
   LaunchCfg c{num_sms(), tm, &g_launches};
@@ -248,7 +249,7 @@ ss_status semisort_common(int op, ss_type kt, ss_type vt, const void* keys, cons
   w.has_vals = vals != nullptr;
   cudaStream_t st = reinterpret_cast<cudaStream_t>(stream);
   PhaseTimer* tm = timer_for(opt, st);
-  cudaError_t e = dispatch(op, kt, vt, P, w, st, tm);
+  cudaError_t e = dispatch(op, kt, vals ? (int)vt : 2, P, w, st, tm);
   if (e == cudaErrorNotSupported) return SS_ERR_UNSUPPORTED;
   return e == cudaSuccess ? SS_OK : SS_ERR_CUDA;
 }

@@ -140,62 +140,136 @@ __device__ __forceinline__ uint32_t block_reduce_sum(uint32_t v, uint32_t* tmp) 
 }
 
 // ---------------------------------------------------------------------------
-// Stable block-wide rank by an 8-bit digit.
+// Stable block-wide rank by a DBITS-bit digit without atomics or warp votes.
 //
-// Items are held R per thread in warp-striped order: item r of lane `lane` in
-// warp w has order index w*32*R + r*32 + lane.  On return rank[r] is the
-// item's position in the stable order by digit (ties keep order index).
-// Within a warp, equal digits are found with __match_any_sync and ordered by
-// lane; across rounds the per-warp counters advance in order; across warps a
-// prefix over warps is added.  Atomics never decide a position, so the result
-// is deterministic.  hist: NW*256 uint16 in shared memory; dsum: 256+33 words.
+// T threads hold R items each in blocked order (thread t holds items
+// t*R .. t*R+R-1, so item order = (thread, slot)).  Every thread counts its
+// items in private 16-bit counters, two digits packed per 32-bit word and laid
+// out [digit pair][thread]; one raking exclusive scan over that array in
+// (digit pair, thread) order then gives, per (digit, thread), the number of
+// items with a smaller digit plus the items of the same digit in earlier
+// threads.  Adding the thread's own running count yields the stable rank.
+// The two packed halves are scanned together; each half counts at most T*R
+// items, so T*R must stay below 65536.  A padding word after every 32 keeps
+// both the counting and the raking phases free of bank conflicts.
 // ---------------------------------------------------------------------------
-template <int NW, int R>
-__device__ __forceinline__ void block_rank8(const uint32_t (&digit)[R], uint32_t (&rank)[R],
-                                            uint16_t* hist, uint32_t* dsum) {
-  const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
-  uint16_t* my = hist + w * 256;
-  for (int d = lane; d < 256; d += 32) my[d] = 0;
-  __syncwarp();
-  const uint32_t lt = (1u << lane) - 1u;
+template <int T, int R, int DBITS>
+struct BlockRank {
+  static constexpr int D = 1 << DBITS;
+  static constexpr int ROWS = D / 2;
+  static constexpr int WORDS = ROWS * T;
+  static constexpr int RAKE = ROWS;  // words raked per thread
+  static constexpr int PWORDS = WORDS + (WORDS / 32) * 4;
+  static_assert(T * R < 65536, "packed 16-bit counters");
+  static_assert(RAKE % 4 == 0 && RAKE <= 32 && 32 % RAKE == 0, "rake range must stay inside a padded block");
+  struct Smem {
+    alignas(16) uint32_t c[PWORDS];
+    uint32_t dofs[D];
+    uint32_t scan_tmp[33];
+  };
+  // 4 padding words after every 32: keeps 16-byte alignment for the raking
+  // loads and spreads both access patterns over all banks.
+  __device__ __forceinline__ static int pidx(int f) { return f + ((f >> 5) << 2); }
+
+  // Digit of item r: (val[r] >> shift) & (D - 1).
+  __device__ static void rank(Smem& s, const uint32_t (&val)[R], int shift, uint32_t (&out)[R]) {
+    const int t = threadIdx.x;
 #pragma unroll
-  for (int r = 0; r < R; ++r) {
-    const uint32_t d = digit[r];
-    const uint32_t peers = __match_any_sync(kFull, d);
-    const int leader = __ffs(peers) - 1;
-    uint32_t base = 0;
-    if (lane == leader) {
-      base = my[d];
-      my[d] = (uint16_t)(base + __popc(peers));
-    }
-    base = __shfl_sync(kFull, base, leader);
-    rank[r] = base + __popc(peers & lt);
-    __syncwarp();
-  }
-  __syncthreads();
-  // Per digit: exclusive prefix over warps (in place) and the digit total.
-  for (int d = threadIdx.x; d < 256; d += blockDim.x) {
-    uint32_t s = 0;
+    for (int i = 0; i < ROWS; ++i) s.c[pidx(i * T + t)] = 0;
+    uint32_t pre[R];
 #pragma unroll
-    for (int ww = 0; ww < NW; ++ww) {
-      uint32_t c = hist[ww * 256 + d];
-      hist[ww * 256 + d] = (uint16_t)s;
-      s += c;
+    for (int r = 0; r < R; ++r) {
+      const uint32_t d = (val[r] >> shift) & (D - 1);
+      const int idx = pidx((int)(d >> 1) * T + t);
+      const uint32_t sh = (d & 1u) << 4;
+      const uint32_t w = s.c[idx];
+      pre[r] = (w >> sh) & 0xFFFFu;
+      s.c[idx] = w + (1u << sh);
     }
-    dsum[d] = s;
-  }
-  __syncthreads();
-  // Exclusive scan of the 256 digit totals (first 256 threads).
-  {
-    uint32_t v = threadIdx.x < 256 ? dsum[threadIdx.x] : 0;
-    uint32_t tot;
-    uint32_t ex = block_exclusive_scan(v, dsum + 256, &tot);
-    if (threadIdx.x < 256) dsum[threadIdx.x] = ex;
+    __syncthreads();
+    uint4* rk4 = reinterpret_cast<uint4*>(&s.c[pidx(t * RAKE)]);
+    uint32_t sum = 0;
+#pragma unroll
+    for (int j = 0; j < RAKE / 4; ++j) {
+      const uint4 v = rk4[j];
+      sum += v.x + v.y + v.z + v.w;
+    }
+    uint32_t total;
+    uint32_t run = block_exclusive_scan(sum, s.scan_tmp, &total);
+#pragma unroll
+    for (int j = 0; j < RAKE / 4; ++j) {
+      const uint4 v = rk4[j];
+      uint4 o;
+      o.x = run;
+      run += v.x;
+      o.y = run;
+      run += v.y;
+      o.z = run;
+      run += v.z;
+      o.w = run;
+      run += v.w;
+      rk4[j] = o;
+    }
+    __syncthreads();
+    // per-digit offsets: even digit 2i adds the odd-digit totals of rows < i,
+    // odd digit 2i+1 adds the even-digit totals of rows <= i
+    for (int d = t; d < D; d += T) {
+      const int i = d >> 1;
+      if (d & 1) {
+        const uint32_t S1 = (i + 1 < ROWS) ? s.c[pidx((i + 1) * T)] : total;
+        s.dofs[d] = S1 & 0xFFFFu;
+      } else {
+        s.dofs[d] = s.c[pidx(i * T)] >> 16;
+      }
+    }
+    __syncthreads();
+#pragma unroll
+    for (int r = 0; r < R; ++r) {
+      const uint32_t d = (val[r] >> shift) & (D - 1);
+      const uint32_t v = s.c[pidx((int)(d >> 1) * T + t)];
+      out[r] = ((v >> ((d & 1u) << 4)) & 0xFFFFu) + s.dofs[d] + pre[r];
+    }
     __syncthreads();
   }
-#pragma unroll
-  for (int r = 0; r < R; ++r) rank[r] += dsum[digit[r]] + my[digit[r]];
-  __syncthreads();
-}
+};
+
+// Conflict-free index for blocked reads of an array written at ranks.
+__device__ __forceinline__ int bpad(int q) { return q + (q >> 5); }
+
+// ---------------------------------------------------------------------------
+// Records of the temporary arrays (array of structures, so a record is one
+// contiguous access); V = void means keys only.
+// ---------------------------------------------------------------------------
+template <class K, class V>
+struct RecT {
+  K k;
+  V v;
+};
+template <class K>
+struct RecT<K, void> {
+  K k;
+};
+
+template <class V>
+struct ValT {
+  using type = V;
+};
+template <>
+struct ValT<void> {
+  using type = uint32_t;  // placeholder, never stored
+};
+
+// Bucketing hash of one recursion level: multiply-shift (Dietzfelbinger et
+// al.) with a seeded odd multiplier per level; the light bucket is the top
+// lbits bits (Sec. 3.1 takes the bucket from hash bits; a fresh multiplier
+// per level plays the role of the next hash function of the family).
+template <class K>
+__device__ __forceinline__ uint64_t fold_key(const K& k);
+template <>
+__device__ __forceinline__ uint64_t fold_key<uint32_t>(const uint32_t& k) { return k; }
+template <>
+__device__ __forceinline__ uint64_t fold_key<uint64_t>(const uint64_t& k) { return k; }
+template <>
+__device__ __forceinline__ uint64_t fold_key<k128>(const k128& k) { return k.lo ^ mix64(k.hi); }
 
 }  // namespace ss

@@ -6,8 +6,9 @@ namespace ss {
 cudaError_t run_u64(int op, int vt, const Plan& P, const Work& w, cudaStream_t st, const LaunchCfg& c) {
   switch (op) {
     case kOpEqual:
-      return vt == 0 ? launch_pipeline<uint64_t, uint32_t, kOpEqual>(P, w, st, c)
-                     : launch_pipeline<uint64_t, uint64_t, kOpEqual>(P, w, st, c);
+      return vt == 0   ? launch_pipeline<uint64_t, uint32_t, kOpEqual>(P, w, st, c)
+             : vt == 1 ? launch_pipeline<uint64_t, uint64_t, kOpEqual>(P, w, st, c)
+                       : launch_pipeline<uint64_t, void, kOpEqual>(P, w, st, c);
     default:
       return cudaErrorNotSupported;
   }

@@ -13,42 +13,35 @@ static cudaError_t set_smem(F* f, size_t bytes) {
   return cudaFuncSetAttribute(f, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes);
 }
 
-// Buffer roles.  semisort: level 0 reads the input and writes T; level 1
-// reads T and writes the output; and so on (the swap of Sec. 3.4, so records
-// move twice in the common two-level case).  Heavy records go straight to the
-// output array whenever that array is not being read at the same level.
-// collect-reduce / histogram alternate between T and T2 and never move heavy
-// records.
+// Buffer roles.  Level 0 reads the caller's input (structure of arrays) and
+// writes light records to T; level l >= 1 reads T or T2 (records) and writes
+// the other one, so records move once per level (the swap of Sec. 3.4).
+// Heavy records go straight to the output whenever the output is not being
+// read at that level; otherwise (in-place level 0) they stay in T and a copy
+// item moves them later.  collect-reduce / histogram never move heavy records.
 template <int OP>
 static LevelBufs level_bufs(const Work& w, int level) {
   LevelBufs b;
   b.level = level;
-  b.salt = level_salt(w.seed, level);
-  auto k_of = [&](uint32_t id) -> void* {
-    return id == kBufIn ? const_cast<void*>(w.in_k) : id == kBufT ? w.t_k : id == kBufOut ? w.out_k : w.t2_k;
-  };
-  auto v_of = [&](uint32_t id) -> void* {
-    return id == kBufIn ? const_cast<void*>(w.in_v) : id == kBufT ? w.t_v : id == kBufOut ? w.out_v : w.t2_v;
-  };
-  uint32_t src_id, dst_id, hdst_id;
-  if (OP == kOpEqual || OP == kOpLess) {
-    dst_id = (level % 2 == 0) ? kBufT : kBufOut;
-    src_id = level == 0 ? kBufIn : ((level - 1) % 2 == 0 ? kBufT : kBufOut);
-    const bool src_is_out = src_id == kBufOut || (src_id == kBufIn && w.in_k == w.out_k);
-    hdst_id = src_is_out ? dst_id : kBufOut;
-  } else {
-    dst_id = (level % 2 == 0) ? kBufT : kBufT2;
-    src_id = level == 0 ? kBufIn : ((level - 1) % 2 == 0 ? kBufT : kBufT2);
-    hdst_id = dst_id;
-  }
-  b.src_k = k_of(src_id);
-  b.src_v = v_of(src_id);
-  b.dst_k = k_of(dst_id);
-  b.dst_v = v_of(dst_id);
-  b.hdst_k = k_of(hdst_id);
-  b.hdst_v = v_of(hdst_id);
+  const uint32_t src_id = level == 0 ? (uint32_t)kBufIn : (level % 2 == 1 ? (uint32_t)kBufT : (uint32_t)kBufT2);
+  const uint32_t dst_id = level % 2 == 0 ? (uint32_t)kBufT : (uint32_t)kBufT2;
+  b.src_k = level == 0 ? w.in_k : (src_id == kBufT ? w.t_k : w.t2_k);
+  b.src_v = level == 0 ? w.in_v : nullptr;
+  b.src_aos = level == 0 ? 0u : 1u;
+  b.dst = dst_id == kBufT ? w.t_k : w.t2_k;
   b.dst_id = dst_id;
-  b.hdst_id = hdst_id;
+  const bool out_is_read = level == 0 && w.in_k == w.out_k;
+  if ((OP == kOpEqual || OP == kOpLess) && !out_is_read) {
+    b.hdst_k = w.out_k;
+    b.hdst_v = w.out_v;
+    b.hdst_aos = 0;
+    b.hdst_id = kBufOut;
+  } else {
+    b.hdst_k = b.dst;
+    b.hdst_v = nullptr;
+    b.hdst_aos = 1;
+    b.hdst_id = dst_id;
+  }
   return b;
 }
 
@@ -56,13 +49,13 @@ template <class K, class V, int OP>
 cudaError_t launch_pipeline(const Plan& P, const Work& w, cudaStream_t st, const LaunchCfg& cfg) {
   PhaseTimer* tm = cfg.timer;
   const int nsm = cfg.num_sms;
-  const size_t dist_smem = sizeof(DistSmem<K>);
-  const size_t ref_smem = sizeof(RefSmem<K>);
+  const size_t dist_smem = sizeof(DistSmem<K, V>);
+  const size_t ref_smem = sizeof(RefSmem<K, V>);
   cudaError_t e;
   if ((e = set_smem(k_distribute<K, V, OP>, dist_smem)) != cudaSuccess) return e;
   if ((e = set_smem(k_finish_equal<K, V>, ref_smem)) != cudaSuccess) return e;
   const uint32_t s_cap_max = P.s1 > P.s2 ? P.s1 : P.s2;
-  if ((e = set_smem(k_sample<K>, (size_t)s_cap_max * sizeof(K))) != cudaSuccess) return e;
+  if ((e = set_smem(k_sample<K, V>, (size_t)s_cap_max * sizeof(K))) != cudaSuccess) return e;
 
   int& nl = *cfg.launches;
   k_init<<<1, 32, 0, st>>>(w);
@@ -77,13 +70,13 @@ cudaError_t launch_pipeline(const Plan& P, const Work& w, cudaStream_t st, const
       k_plan<<<1, 1024, 0, st>>>(w, level);
       if (tm) tm->mark(level == 0 ? "plan.L0" : "plan.L1+");
       const uint32_t s_cap = level == 0 ? P.s1 : P.s2;
-      k_sample<K><<<cap(segs, nsm * 2), 1024, (size_t)s_cap * sizeof(K), st>>>(w, lb, s_cap);
+      k_sample<K, V><<<cap(segs, nsm * 2), 1024, (size_t)s_cap * sizeof(K), st>>>(w, lb, s_cap);
       if (tm) tm->mark(level == 0 ? "sample.L0" : "sample.L1+");
-      k_count<K, OP><<<cap(tiles, nsm * 4), 512, 0, st>>>(w, lb);
+      k_count<K, V, OP><<<cap(tiles, nsm * 4), kCountThreads, 0, st>>>(w, lb);
       if (tm) tm->mark(level == 0 ? "count.L0" : "count.L1+");
       k_scan<OP><<<cap(segs, nsm * 2), 1024, 0, st>>>(w, lb);
       if (tm) tm->mark(level == 0 ? "scan.L0" : "scan.L1+");
-      k_distribute<K, V, OP><<<cap(tiles, nsm * 2), kDistThreads, dist_smem, st>>>(w, lb);
+      k_distribute<K, V, OP><<<cap(tiles, nsm * 2), kDT, dist_smem, st>>>(w, lb);
       if (tm) tm->mark(level == 0 ? "distribute.L0" : "distribute.L1+");
       k_scan_items<<<1, 1024, 0, st>>>(w, level);
       k_emit<OP><<<cap(segs, nsm * 2), 1024, 0, st>>>(w, lb);
@@ -92,7 +85,7 @@ cudaError_t launch_pipeline(const Plan& P, const Work& w, cudaStream_t st, const
     }
   }
   if (OP == kOpEqual) {
-    k_finish_equal<K, V><<<nsm * 2, kRefThreads, ref_smem, st>>>(w);
+    k_finish_equal<K, V><<<nsm * 2, kRT, ref_smem, st>>>(w);
     ++nl;
     if (tm) tm->mark("refine");
   }

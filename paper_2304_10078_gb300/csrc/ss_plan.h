@@ -12,8 +12,9 @@
 namespace ss {
 
 constexpr int kMaxLevels = 4;          // recursion levels (Algorithm 1) before the depth error
-constexpr int kMaxLightLog2 = 11;      // n_L <= 2048 per segment
-constexpr uint32_t kMaxHeavy = 1024;   // heavy keys per segment
+constexpr int kMaxLightLog2 = 9;       // n_L <= 512 per segment
+constexpr uint32_t kMaxHeavy = 512;    // heavy keys per segment
+constexpr uint32_t kMaxBuckets = 1024; // n_L + heavy: bucket ids fit two 5-bit rank passes
 constexpr uint32_t kCopyChunk = 1u << 16;  // records per copy item
 
 // Operations.
@@ -40,6 +41,7 @@ struct Seg {
   uint32_t cnt_fin;    // finish items emitted
   uint32_t cnt_next;   // next-level segments emitted
   uint32_t pad;
+  uint64_t mult;       // odd multiplier of this segment's bucketing hash
 };
 
 struct Tile {
@@ -96,7 +98,7 @@ struct Work {
   Tile* tiles[kMaxLevels];
   uint32_t* C[kMaxLevels];
   void* hkeys[kMaxLevels];       // heavy keys (sorted), per segment at bbase
-  uint32_t* htab[kMaxLevels];    // heavy hash table: heavy index or kEmpty, per segment at bbase (2 n_L slots)
+  uint16_t* htab[kMaxLevels];    // heavy hash table: heavy index or 0xFFFF, per segment at 2*bbase (4 hcap slots)
   uint32_t* bsize[kMaxLevels];   // bucket totals
   uint32_t* boff[kMaxLevels];    // bucket offsets within segment
   uint64_t* hpart[kMaxLevels];   // collect-reduce heavy partials (nbcap x ntiles layout, rows >= n_L)
