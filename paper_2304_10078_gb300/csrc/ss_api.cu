@@ -73,37 +73,46 @@ ss_status make_plan(int op, int kt, int vt, uint64_t n, const ss_options* opt, i
   if (P->kbytes == 16) s1 = std::min<uint32_t>(s1, 8192);
   P->s1 = s1;
   P->s2 = 8192;
-  // level 0
+  const bool less = op == SS_OP_SEMISORT_LESS;
+  const bool red = op == SS_OP_COLLECT_REDUCE || op == SS_OP_HISTOGRAM;
+  // level 0: one segment; bucket rows per segment are n_L + n_H,cap (hash
+  // buckets) or 4 n_L (semisort_<: 2q + 1 ids for q < 2 n_L boundaries)
+  const uint32_t nl0 = 1u << (less ? std::min<uint32_t>(lb1, kMaxLightLog2 - 1) : lb1);
+  const uint32_t rows0 = less ? 4 * nl0 : nl0 + std::min<uint32_t>(nl0, kMaxHeavy);
   P->seg_cap[0] = 1;
   P->tile_cap[0] = (uint32_t)((n + P->l1 - 1) / P->l1);
-  P->bucket_cap[0] = 2u << lb1;
-  P->c_cap[0] = (uint64_t)((1u << lb1) + std::min<uint32_t>(1u << lb1, kMaxHeavy)) * P->tile_cap[0];
+  P->bucket_cap[0] = rows0;
+  P->c_cap[0] = (uint64_t)rows0 * P->tile_cap[0];
   for (int l = 1; l < kMaxLevels; ++l) {
     const uint64_t segs = n / (alpha + 1) + 1;
     P->seg_cap[l] = (uint32_t)segs;
     P->tile_cap[l] = (uint32_t)((n + l2 - 1) / l2 + segs);
-    // a segment of m > alpha records has n_L < 4m/alpha + 2 light buckets,
-    // so 2 n_L rows < 8m/alpha + 4 and the sum over segments < 12n/alpha
-    P->bucket_cap[l] = (uint32_t)(12 * n / alpha + 64);
-    P->c_cap[l] = (uint64_t)kMaxBuckets * ((n + l2 - 1) / l2) + 12 * n / alpha + 64;
+    // a segment of m > alpha records has n_L < 4m/alpha + 2 light buckets, so
+    // its rows (at most 2 n_L, or 4 n_L for semisort_<) sum over the segments
+    // (fewer than n/alpha of them) to below 12n/alpha (24n/alpha)
+    P->bucket_cap[l] = (uint32_t)((less ? 24 : 12) * n / alpha + 64);
+    // rows x subarrays: sum over segments of rows * (m/l2 + 1)
+    P->c_cap[l] = (uint64_t)kMaxBuckets * ((n + l2 - 1) / l2) + P->bucket_cap[l];
   }
   uint64_t items = n / kCopyChunk + 16;
   for (int l = 0; l < kMaxLevels; ++l) items += P->bucket_cap[l];
   P->item_cap = (uint32_t)std::min<uint64_t>(items, 0xFFFFFFF0ull);
   // layout: control block first, so status calls can find it without a plan
   size_t o = al(sizeof(Ctrl));
-  // temporaries T and T2 hold records (key, value) as array of structures
-  const bool need_t = n > alpha;
+  // temporaries T and T2 hold records (key, value) as array of structures;
+  // collect-reduce / histogram always need T (compacted base-case outputs)
+  const bool multi = n > alpha;
+  const bool need_t = multi || red;
   const size_t ralign = std::max(P->kbytes == 16 ? 16 : P->kbytes, P->vbytes);
   const size_t recbytes = (P->kbytes + P->vbytes + ralign - 1) / ralign * ralign;
   P->off_tk = o;
   o = al(o + (need_t ? n * recbytes : 0));
   P->off_tv = o;
   P->off_t2k = o;
-  o = al(o + (need_t ? n * recbytes : 0));
+  o = al(o + (multi ? n * recbytes : 0));
   P->off_t2v = o;
   for (int l = 0; l < kMaxLevels; ++l) {
-    if (!need_t) {
+    if (!multi) {
       P->seg_cap[l] = P->tile_cap[l] = P->bucket_cap[l] = 0;
       P->c_cap[l] = 0;
     }
@@ -124,18 +133,21 @@ ss_status make_plan(int op, int kt, int vt, uint64_t n, const ss_options* opt, i
     P->off_hpart[l] = o;
     o = al(o + (op == SS_OP_COLLECT_REDUCE ? (size_t)P->c_cap[l] * 8 : 0));
     P->off_split[l] = o;
-    o = al(o + (op == SS_OP_SEMISORT_LESS ? (size_t)P->bucket_cap[l] * P->kbytes : 0));
+    o = al(o + (less ? (size_t)P->bucket_cap[l] * P->kbytes : 0));
   }
-  if (!need_t) P->item_cap = 1;
+  if (!multi) P->item_cap = 1;
   P->off_items = o;
   o = al(o + (size_t)P->item_cap * sizeof(Item));
-  const bool red = op == SS_OP_COLLECT_REDUCE || op == SS_OP_HISTOGRAM;
   P->off_item_out = o;
   o = al(o + (red ? (size_t)P->item_cap * 8 : 0));
   P->off_item_pos = o;
   o = al(o + (red ? (size_t)P->item_cap * 8 : 0));
   P->off_block_sums = o;
-  o = al(o + (red ? 8192 * 8 : 0));
+  o = al(o + (red ? ((size_t)P->item_cap / 4096 + 2) * 8 : 0));
+  P->off_item_aux = o;
+  o = al(o + (op == SS_OP_COLLECT_REDUCE ? (size_t)P->item_cap * 8 : 0));
+  P->off_scratch32 = o;
+  o = al(o + (op == SS_OP_HISTOGRAM ? (size_t)n * 4 : 0));
   P->off_ctrl = 0;
   P->total = o;
   return SS_OK;
@@ -175,6 +187,8 @@ void fill_work(const Plan& P, void* ws, Work* w) {
   w->item_out = reinterpret_cast<uint64_t*>(b + P.off_item_out);
   w->item_pos = reinterpret_cast<uint64_t*>(b + P.off_item_pos);
   w->block_sums = reinterpret_cast<uint64_t*>(b + P.off_block_sums);
+  w->item_aux = reinterpret_cast<uint64_t*>(b + P.off_item_aux);
+  w->scratch32 = reinterpret_cast<uint32_t*>(b + P.off_scratch32);
   w->ctrl = reinterpret_cast<Ctrl*>(b + P.off_ctrl);
 }
 
@@ -254,6 +268,59 @@ ss_status semisort_common(int op, ss_type kt, ss_type vt, const void* keys, cons
   return e == cudaSuccess ? SS_OK : SS_ERR_CUDA;
 }
 
+// collect-reduce (vals != NULL) and histogram (vals == NULL, counts in sums).
+ss_status reduce_common(int op, ss_type kt, const void* keys, const uint64_t* vals, void* ukeys, void* sums,
+                        uint64_t capacity, uint64_t* d_num_unique, uint64_t n, void* ws, size_t ws_bytes,
+                        const ss_options* opt, ss_stream_t stream) {
+  if (!d_num_unique || (reinterpret_cast<uintptr_t>(d_num_unique) & 7)) return SS_ERR_INVALID_ARG;
+  cudaStream_t st = reinterpret_cast<cudaStream_t>(stream);
+  const int kb1 = kbytes_of(kt);
+  if (!kb1) return SS_ERR_INVALID_ARG;
+  if (n == 0) {
+    if (ws && aligned16(ws) && ws_bytes >= sizeof(Ctrl)) {
+      if (cudaMemsetAsync(ws, 0, sizeof(Ctrl), st) != cudaSuccess) return SS_ERR_CUDA;
+    }
+    return cudaMemsetAsync(d_num_unique, 0, 8, st) == cudaSuccess ? SS_OK : SS_ERR_CUDA;
+  }
+  if (!keys || !ukeys || !sums || !ws) return SS_ERR_INVALID_ARG;
+  if (op == kOpReduce && !vals) return SS_ERR_INVALID_ARG;
+  if (!aligned16(keys) || !aligned16(ukeys) || !aligned16(sums) || !aligned16(ws) || (vals && !aligned16(vals)))
+    return SS_ERR_INVALID_ARG;
+  Plan P;
+  ss_status s = make_plan(op, kt, SS_U64, n, opt, num_sms(), &P);
+  if (s != SS_OK) return s;
+  if (ws_bytes < P.total) return SS_ERR_WORKSPACE_TOO_SMALL;
+  const uint64_t sb = op == kOpReduce ? 8 : 4;
+  Range rk{(uintptr_t)keys, (uintptr_t)keys + n * kb1};
+  Range rv{(uintptr_t)vals, (uintptr_t)vals + (vals ? n * 8 : 0)};
+  Range ru{(uintptr_t)ukeys, (uintptr_t)ukeys + capacity * kb1};
+  Range rs{(uintptr_t)sums, (uintptr_t)sums + capacity * sb};
+  Range rw{(uintptr_t)ws, (uintptr_t)ws + P.total};
+  Range rn{(uintptr_t)d_num_unique, (uintptr_t)d_num_unique + 8};
+  const Range outs[3] = {ru, rs, rn};
+  for (const Range& o : outs) {
+    if (overlap(o, rk) || overlap(o, rw) || (vals && overlap(o, rv))) return SS_ERR_INVALID_ARG;
+  }
+  if (overlap(ru, rs) || overlap(ru, rn) || overlap(rs, rn)) return SS_ERR_INVALID_ARG;
+  if (overlap(rw, rk) || (vals && overlap(rw, rv))) return SS_ERR_INVALID_ARG;
+  Work w;
+  memset(&w, 0, sizeof(w));
+  fill_work(P, ws, &w);
+  w.seed = opt ? opt->seed : 0;
+  w.in_k = keys;
+  w.in_v = vals;
+  w.out_k = ukeys;
+  w.out_v = nullptr;
+  w.has_vals = vals != nullptr;
+  w.sums_out = sums;
+  w.num_unique = d_num_unique;
+  w.out_capacity = capacity;
+  PhaseTimer* tm = timer_for(opt, st);
+  cudaError_t e = dispatch(op, kt, op == kOpReduce ? (int)SS_U64 : 2, P, w, st, tm);
+  if (e == cudaErrorNotSupported) return SS_ERR_UNSUPPORTED;
+  return e == cudaSuccess ? SS_OK : SS_ERR_CUDA;
+}
+
 __global__ void k_hash_u64(const uint64_t* k, uint64_t* o, uint64_t n, uint64_t salt) {
   for (uint64_t i = blockIdx.x * (uint64_t)blockDim.x + threadIdx.x; i < n; i += (uint64_t)gridDim.x * blockDim.x)
     o[i] = mix64(k[i] ^ salt);
@@ -288,14 +355,19 @@ ss_status semisort_less(ss_type key_type, ss_type val_type, const void* keys, co
                          stream);
 }
 
-ss_status collect_reduce(ss_type, const void*, const uint64_t*, void*, uint64_t*, uint64_t, uint64_t*, uint64_t,
-                         void*, size_t, const ss_options*, ss_stream_t) {
-  return SS_ERR_UNSUPPORTED;
+ss_status collect_reduce(ss_type key_type, const void* keys, const uint64_t* vals, void* ukeys_out,
+                         uint64_t* sums_out, uint64_t capacity, uint64_t* d_num_unique, uint64_t n, void* ws,
+                         size_t ws_bytes, const ss_options* opt, ss_stream_t stream) {
+  if (n && !vals) return SS_ERR_INVALID_ARG;
+  return reduce_common(kOpReduce, key_type, keys, vals, ukeys_out, sums_out, capacity, d_num_unique, n, ws,
+                       ws_bytes, opt, stream);
 }
 
-ss_status histogram(ss_type, const void*, void*, uint32_t*, uint64_t, uint64_t*, uint64_t, void*, size_t,
-                    const ss_options*, ss_stream_t) {
-  return SS_ERR_UNSUPPORTED;
+ss_status histogram(ss_type key_type, const void* keys, void* ukeys_out, uint32_t* counts_out, uint64_t capacity,
+                    uint64_t* d_num_unique, uint64_t n, void* ws, size_t ws_bytes, const ss_options* opt,
+                    ss_stream_t stream) {
+  return reduce_common(kOpHist, key_type, keys, nullptr, ukeys_out, counts_out, capacity, d_num_unique, n, ws,
+                       ws_bytes, opt, stream);
 }
 
 ss_status ss_last_device_error(void* ws, ss_stream_t stream, int* code) {

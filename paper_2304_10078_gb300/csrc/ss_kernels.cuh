@@ -91,6 +91,42 @@ __device__ __forceinline__ uint32_t bucket_of(const K& k, uint64_t mult, uint32_
   return b;
 }
 
+// semisort_< bucket of key k: with q sorted boundaries bnd[] (splitters and
+// heavy keys, flags[i] = 1 for a heavy key), u = #boundaries <= k; range
+// bucket 2u holds bnd[u-1] < k < bnd[u] (or bnd[u-1] <= k if bnd[u-1] is not
+// heavy), equality bucket 2u-1 holds k == bnd[u-1] for a heavy boundary.  Bucket
+// ids therefore increase with the key, so concatenating the buckets in id order
+// is a key-ordered partition (samplesort with equality buckets).
+template <class K>
+__device__ __forceinline__ uint32_t bucket_less(const K& k, const K* bnd, const uint16_t* flags, uint32_t q) {
+  uint32_t lo = 0, hi = q;  // upper bound: first boundary > k
+  while (lo < hi) {
+    const uint32_t mid = (lo + hi) >> 1;
+    if (KeyT<K>::lt(k, bnd[mid]))
+      hi = mid;
+    else
+      lo = mid + 1;
+  }
+  if (lo > 0 && flags[lo - 1] && KeyT<K>::eq(bnd[lo - 1], k)) return 2 * lo - 1;
+  return 2 * lo;
+}
+
+// Whether bucket b holds a single heavy key (final after distribution).
+template <int OP>
+__device__ __forceinline__ bool is_heavy(uint32_t b, uint32_t nl) {
+  return OP == kOpLess ? (b & 1u) != 0 : b >= nl;
+}
+
+// Bucket of a key in segment sg (its tables already in shared memory).
+template <class K, int OP>
+__device__ __forceinline__ uint32_t bucket_in(const K& k, const Seg& sg, const K* hk, const uint16_t* ht,
+                                              uint32_t tmask) {
+  if constexpr (OP == kOpLess)
+    return bucket_less<K>(k, hk, ht, sg.nh);
+  else
+    return bucket_of<K>(k, sg.mult, sg.lbits, sg.nh, hk, ht, tmask);
+}
+
 // ----------------------------------------------------------------------------
 // init: reset the control block and seed level 0 (or a single base case).
 // ----------------------------------------------------------------------------
@@ -128,6 +164,7 @@ __global__ void k_init(Work w) {
 // plan: per segment of level `level`, pick n_L, cut it into subarrays, and
 // lay out its rows of the count matrix.  One CTA.
 // ----------------------------------------------------------------------------
+template <int OP>
 __global__ void __launch_bounds__(1024) k_plan(Work w, int level) {
   __shared__ uint64_t tmp64[33];
   __shared__ uint64_t carry[3];
@@ -152,14 +189,17 @@ __global__ void __launch_bounds__(1024) k_plan(Work w, int level) {
         lb = want <= 2 ? 1u : (uint32_t)(64 - __clzll(want - 1));
         lb = lb > (uint32_t)kMaxLightLog2 ? (uint32_t)kMaxLightLog2 : lb;
       }
+      if (OP == kOpLess && lb > kMaxLightLog2 - 1) lb = kMaxLightLog2 - 1;
       const uint32_t nl = 1u << lb;
       sg.lbits = lb;
-      sg.nbcap = nl + hcap_of(lb);
+      // semisort_<: q <= (n_L - 1) + n_L boundaries give 2q + 1 < 4 n_L bucket ids
+      sg.nbcap = OP == kOpLess ? 4 * nl : nl + hcap_of(lb);
       sg.nh = 0;
+      sg.nb = nl;
       sg.mult = seg_mult(w.seed, level, sg.start);
       sg.ntiles = (uint32_t)((sg.len + (uint64_t)l - 1) / l);
       nt = sg.ntiles;
-      nb2 = 2ull * nl;
+      nb2 = sg.nbcap;
       cc = (uint64_t)sg.nbcap * sg.ntiles;
     }
     uint64_t tt, tb, tc;
@@ -209,9 +249,12 @@ __global__ void __launch_bounds__(1024) k_plan(Work w, int level) {
 // seeded random positions, sort them, and make every key seen at least
 // tau = |S| / n_H,cap times heavy (a key expected to fill at least one light
 // bucket).  Heavy keys get ids in ascending key order (deterministic) and an
-// open-addressing lookup table with 4 slots per heavy key.
+// open-addressing lookup table with 4 slots per heavy key.  semisort_< also
+// takes n_L - 1 splitters at evenly spaced sample ranks and merges them with
+// the heavy keys into one sorted boundary list (equality buckets for heavy
+// keys, samplesort-style).
 // ----------------------------------------------------------------------------
-template <class K, class V>
+template <class K, class V, int OP>
 __global__ void __launch_bounds__(1024) k_sample(Work w, LevelBufs lb, uint32_t s_cap) {
   extern __shared__ __align__(16) unsigned char smem[];
   K* S = reinterpret_cast<K*>(smem);
@@ -278,19 +321,69 @@ __global__ void __launch_bounds__(1024) k_sample(Work w, LevelBufs lb, uint32_t 
     }
     __syncthreads();
     uint16_t* ht = w.htab[lb.level] + 2ull * sg.bbase;
-    for (uint32_t t = threadIdx.x; t < tsize; t += blockDim.x) ht[t] = (uint16_t)(tab[t] == kEmpty ? 0xFFFFu : tab[t]);
-    if (threadIdx.x == 0) {
-      w.segs[lb.level][s].nh = nh;
-      if (lb.level == 0) w.ctrl->stats[7] = nh;
+    if constexpr (OP == kOpLess) {
+      if (threadIdx.x == 0) {
+        // merge splitters S[j S_n / n_L] (deduplicated) with the heavy keys
+        const uint32_t nl = 1u << sg.lbits;
+        K* bnd = reinterpret_cast<K*>(w.splitters[lb.level]) + sg.bbase;
+        uint32_t q = 0, j = 1, hi = 0;
+        bool have_last = false;
+        K last = S[0];
+        while (j < nl || hi < nh) {
+          K cand;
+          bool heavy;
+          if (j < nl && (hi >= nh || KeyT<K>::lt(S[(uint64_t)j * S_n / nl], hk[hi]))) {
+            cand = S[(uint64_t)j * S_n / nl];
+            heavy = false;
+            ++j;
+          } else if (j < nl && KeyT<K>::eq(S[(uint64_t)j * S_n / nl], hk[hi])) {
+            cand = hk[hi];
+            heavy = true;
+            ++j;
+            ++hi;
+          } else {
+            cand = hk[hi];
+            heavy = true;
+            ++hi;
+          }
+          if (have_last && KeyT<K>::eq(cand, last)) {
+            if (heavy) ht[q - 1] = 1;
+            continue;
+          }
+          bnd[q] = cand;
+          ht[q] = heavy ? 1 : 0;
+          ++q;
+          last = cand;
+          have_last = true;
+        }
+        w.segs[lb.level][s].nh = q;
+        w.segs[lb.level][s].nb = 2 * q + 1;
+        if (lb.level == 0) w.ctrl->stats[7] = nh;
+      }
+    } else {
+      for (uint32_t t = threadIdx.x; t < tsize; t += blockDim.x) ht[t] = (uint16_t)(tab[t] == kEmpty ? 0xFFFFu : tab[t]);
+      if (threadIdx.x == 0) {
+        w.segs[lb.level][s].nh = nh;
+        w.segs[lb.level][s].nb = (1u << sg.lbits) + nh;
+        if (lb.level == 0) w.ctrl->stats[7] = nh;
+      }
     }
     __syncthreads();
   }
 }
 
-// Load a segment's heavy keys and table into shared memory.
-template <class K>
+// Load a segment's heavy keys and table (semisort_<: boundaries and flags)
+// into shared memory.
+template <class K, int OP>
 __device__ __forceinline__ void load_heavy(const Work& w, int level, const Seg& sg, K* hk, uint16_t* ht) {
-  if (sg.nh) {
+  if (OP == kOpLess) {
+    const K* gb = reinterpret_cast<const K*>(w.splitters[level]) + sg.bbase;
+    const uint16_t* gf = w.htab[level] + 2ull * sg.bbase;
+    for (uint32_t i = threadIdx.x; i < sg.nh; i += blockDim.x) {
+      hk[i] = gb[i];
+      ht[i] = gf[i];
+    }
+  } else if (sg.nh) {
     const uint32_t tsize = 4 * hcap_of(sg.lbits);
     const K* ghk = reinterpret_cast<const K*>(w.hkeys[level]) + sg.bbase;
     const uint16_t* ght = w.htab[level] + 2ull * sg.bbase;
@@ -318,9 +411,9 @@ __global__ void __launch_bounds__(kCountThreads) k_count(Work w, LevelBufs lb) {
     const Tile tl = w.tiles[lb.level][t];
     const Seg sg = w.segs[lb.level][tl.seg];
     const uint32_t nl = 1u << sg.lbits;
-    const uint32_t nb = nl + sg.nh;
+    const uint32_t nb = sg.nb;
     const uint32_t tmask = 4 * hcap_of(sg.lbits) - 1;
-    load_heavy<K>(w, lb.level, sg, hk, ht);
+    load_heavy<K, OP>(w, lb.level, sg, hk, ht);
     for (uint32_t b = threadIdx.x; b < nb; b += blockDim.x) hist[b] = 0;
     if (OP == kOpReduce)
       for (uint32_t b = threadIdx.x; b < sg.nh; b += blockDim.x) hsum[b] = 0;
@@ -338,7 +431,7 @@ __global__ void __launch_bounds__(kCountThreads) k_count(Work w, LevelBufs lb) {
       for (int u = 0; u < U; ++u) {
         const uint32_t i = i0 + u * blockDim.x + threadIdx.x;
         if (i < tl.len) {
-          const uint32_t b = bucket_of<K>(key[u], sg.mult, sg.lbits, sg.nh, hk, ht, tmask);
+          const uint32_t b = bucket_in<K, OP>(key[u], sg, hk, ht, tmask);
           atomicAdd(&hist[b], 1u);
           if constexpr (OP == kOpReduce) {
             if (b >= nl) {
@@ -380,7 +473,7 @@ __device__ __forceinline__ void items_of_bucket(uint32_t b, uint32_t nl, uint32_
   *nf = 0;
   *nx = 0;
   if (!sz) return;
-  if (b >= nl) {
+  if (is_heavy<OP>(b, nl)) {
     if (OP == kOpReduce || OP == kOpHist)
       *nf = 1;
     else if (hdst_id != kBufOut)
@@ -394,10 +487,16 @@ __device__ __forceinline__ void items_of_bucket(uint32_t b, uint32_t nl, uint32_
 // alpha records each, merged greedily in bucket order while the run stays
 // within alpha records.  Equal keys never straddle buckets, so refining a
 // window is the same as refining each of its buckets (Sec. 3.3) one after
-// the other.  Run by one thread; writes the items when `items` is non-null.
+// the other; for semisort_< the buckets are key ranges in increasing order, so
+// sorting a window is the same as sorting its buckets in turn.  A non-empty
+// heavy bucket ends the current window (its records sit between light ones in
+// the semisort_< layout).  Run by one thread; writes the items when `items`
+// is non-null.
+template <int OP>
 __device__ __forceinline__ uint32_t refine_windows(const uint32_t* bsize, const uint32_t* boff, uint32_t nl,
-                                                   uint32_t alpha, bool last, uint64_t seg_start, uint32_t buf,
-                                                   int level, Item* items, uint32_t first, uint32_t cap) {
+                                                   uint32_t nb, uint32_t alpha, bool last, uint64_t seg_start,
+                                                   uint32_t buf, int level, Item* items, uint32_t first,
+                                                   uint32_t cap) {
   uint32_t cnt = 0, wstart = 0, wlen = 0;
   bool open = false;
   auto flush = [&]() {
@@ -414,9 +513,13 @@ __device__ __forceinline__ uint32_t refine_windows(const uint32_t* bsize, const 
     ++cnt;
     open = false;
   };
-  for (uint32_t b = 0; b < nl; ++b) {
+  for (uint32_t b = 0; b < nb; ++b) {
     const uint32_t sz = bsize[b];
     if (sz == 0) continue;
+    if (is_heavy<OP>(b, nl)) {
+      if (open) flush();
+      continue;
+    }
     if (sz > alpha) {
       if (open) flush();
       if (last) {  // no level left: an oversized base case (reported as a depth error)
@@ -455,7 +558,7 @@ __global__ void __launch_bounds__(1024) k_scan(Work w, LevelBufs lb) {
       continue;
     }
     const uint32_t nl = 1u << sg.lbits;
-    const uint32_t nb = nl + sg.nh;
+    const uint32_t nb = sg.nb;
     uint32_t* C = w.C[lb.level] + sg.cbase;
     uint32_t* bsize = w.bsize[lb.level] + sg.bbase;
     uint32_t* boff = w.boff[lb.level] + sg.bbase;
@@ -478,7 +581,7 @@ __global__ void __launch_bounds__(1024) k_scan(Work w, LevelBufs lb) {
     for (uint32_t b0 = 0; b0 < nb; b0 += blockDim.x) {
       const uint32_t b = b0 + threadIdx.x;
       const uint32_t sz = b < nb ? bsize[b] : 0;
-      const bool heavy = b >= nl;
+      const bool heavy = is_heavy<OP>(b, nl);
       // Collect-reduce and histogram never move heavy records (Sec. 3.5).
       const uint32_t lay = (heavy && (OP == kOpReduce || OP == kOpHist)) ? 0 : sz;
       uint32_t tot;
@@ -497,8 +600,8 @@ __global__ void __launch_bounds__(1024) k_scan(Work w, LevelBufs lb) {
     const uint32_t tf = block_reduce_sum(nfin, tmp);
     const uint32_t tn = block_reduce_sum(nnext, tmp);
     if (threadIdx.x == 0) {
-      const uint32_t nw = refine_windows(bsize, boff, nl, w.alpha, last_level, sg.start, lb.dst_id, lb.level,
-                                         nullptr, 0, 0);
+      const uint32_t nw = refine_windows<OP>(bsize, boff, nl, nb, w.alpha, last_level, sg.start, lb.dst_id,
+                                             lb.level, nullptr, 0, 0);
       w.segs[lb.level][s].cnt_fin = tf + nw;
       w.segs[lb.level][s].cnt_next = tn;
     }
@@ -554,9 +657,9 @@ __global__ void __launch_bounds__(kDT, 2) k_distribute(Work w, LevelBufs lb) {
     const Tile tl = w.tiles[lb.level][t];
     const Seg sg = w.segs[lb.level][tl.seg];
     const uint32_t nl = 1u << sg.lbits;
-    const uint32_t nb = nl + sg.nh;
+    const uint32_t nb = sg.nb;
     const uint32_t tmask = 4 * hcap_of(sg.lbits) - 1;
-    load_heavy<K>(w, lb.level, sg, sm.hk, sm.ht);
+    load_heavy<K, OP>(w, lb.level, sg, sm.hk, sm.ht);
     {
       const uint32_t* X = w.C[lb.level] + sg.cbase;
       const uint32_t* boff = w.boff[lb.level] + sg.bbase;
@@ -576,7 +679,7 @@ __global__ void __launch_bounds__(kDT, 2) k_distribute(Work w, LevelBufs lb) {
         // invalid slots get the largest bucket id: both 5-bit digits are 31, so they rank last
 #pragma unroll
         for (int r = 0; r < kDR; ++r)
-          bid[r] = c0t + r < clen ? bucket_of<K>(key[r], sg.mult, sg.lbits, sg.nh, sm.hk, sm.ht, tmask)
+          bid[r] = c0t + r < clen ? bucket_in<K, OP>(key[r], sg, sm.hk, sm.ht, tmask)
                                   : (kMaxBuckets - 1);
       }
       DRank::rank(sm.u.a.rk, bid, 0, rk);
@@ -627,7 +730,7 @@ __global__ void __launch_bounds__(kDT, 2) k_distribute(Work w, LevelBufs lb) {
         const uint32_t rel = sm.base[b] + p;
         const uint64_t pos = sg.start + rel;
         const Rec rec = sm.u.stage[p];
-        if (b < nl) {
+        if (!is_heavy<OP>(b, nl)) {
           dst[pos] = rec;
         } else if constexpr (kMoveHeavy) {
           if (lb.hdst_aos) {
@@ -702,14 +805,14 @@ __global__ void __launch_bounds__(1024) k_emit(Work w, LevelBufs lb) {
     const Seg sg = w.segs[lb.level][s];
     if (sg.lbits == 0) continue;
     const uint32_t nl = 1u << sg.lbits;
-    const uint32_t nb = nl + sg.nh;
+    const uint32_t nb = sg.nb;
     const uint32_t* bsize = w.bsize[lb.level] + sg.bbase;
     const uint32_t* boff = w.boff[lb.level] + sg.bbase;
     if (threadIdx.x == 0) {
-      const uint32_t nw = refine_windows(bsize, boff, nl, w.alpha, last_level, sg.start, lb.dst_id, lb.level,
-                                         w.items, sg.fin_off, w.item_cap);
-      for (uint32_t b = 0; b < nl; ++b)
-        if (bsize[b] > w.alpha && last_level) set_error(w.ctrl, 8 /*SS_ERR_DEPTH*/);
+      const uint32_t nw = refine_windows<OP>(bsize, boff, nl, nb, w.alpha, last_level, sg.start, lb.dst_id,
+                                             lb.level, w.items, sg.fin_off, w.item_cap);
+      for (uint32_t b = 0; b < nb; ++b)
+        if (!is_heavy<OP>(b, nl) && bsize[b] > w.alpha && last_level) set_error(w.ctrl, 8 /*SS_ERR_DEPTH*/);
       carry[0] = sg.fin_off + nw;
       carry[1] = sg.next_off;
     }
@@ -717,7 +820,7 @@ __global__ void __launch_bounds__(1024) k_emit(Work w, LevelBufs lb) {
     for (uint32_t b0 = 0; b0 < nb; b0 += blockDim.x) {
       const uint32_t b = b0 + threadIdx.x;
       const uint32_t sz = b < nb ? bsize[b] : 0;
-      const bool heavy = b >= nl;
+      const bool heavy = is_heavy<OP>(b, nl);
       uint32_t nf = 0, nx = 0;
       if (b < nb) items_of_bucket<OP>(b, nl, sz, w.alpha, last_level, lb.hdst_id, &nf, &nx);
       uint32_t tf, tx;
@@ -945,6 +1048,347 @@ __global__ void __launch_bounds__(kRT, 2) k_finish_equal(Work w) {
     __syncthreads();
     for (uint32_t p = tid; p < m; p += kRT) store_out<K, V>(w, it.start + p, sm.u.stage[p]);
     __syncthreads();
+  }
+}
+
+
+// ----------------------------------------------------------------------------
+// finish (semisort_<): the base case of Sec. 3.3 with a comparison sort, and
+// the copy-backs of Sec. 3.4.  A window is sorted in shared memory by (key,
+// position in the window) with Batcher's bitonic network; only 16-bit
+// positions move, keys stay where they were loaded.  The position tie-break
+// makes the order stable, so the output equals a stable sort by key.
+// ----------------------------------------------------------------------------
+template <class K, class V>
+struct LessSmem {
+  union {
+    struct {
+      K keys[kRefMax];
+      uint16_t idx[kRefMax];
+    } s;
+    RecT<K, V> stage[kRefMax];
+  } u;
+  uint16_t fpos[kRefMax];
+};
+
+template <class K, class V>
+__global__ void __launch_bounds__(kRT, 2) k_finish_less(Work w) {
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  LessSmem<K, V>& sm = *reinterpret_cast<LessSmem<K, V>*>(smem_raw);
+  const uint32_t nfin = w.ctrl->nfin;
+  const int tid = threadIdx.x;
+  for (uint32_t itx = blockIdx.x; itx < nfin; itx += gridDim.x) {
+    const Item it = w.items[itx];
+    if (it.kind == kItemCopy) {
+      for (uint32_t i = tid; i < it.len; i += kRT)
+        store_out<K, V>(w, it.start + i, load_rec<K, V>(w, it.buf, it.start + i));
+      if (tid == 0) atomicAdd((unsigned long long*)&w.ctrl->stats[6], (unsigned long long)it.len);
+      continue;
+    }
+    const uint32_t m = it.len;
+    if (m > (uint32_t)kRefMax) {
+      if (tid == 0) set_error(w.ctrl, 8);
+      continue;
+    }
+    uint32_t P = 2;
+    while (P < m) P <<= 1;
+    for (uint32_t c = tid; c < P; c += kRT) {
+      if (c < m)
+        sm.u.s.keys[c] = it.buf == kBufIn ? reinterpret_cast<const K*>(w.in_k)[it.start + c]
+                                          : reinterpret_cast<const RecT<K, V>*>(buf_ptr(w, it.buf))[it.start + c].k;
+      sm.u.s.idx[c] = (uint16_t)c;  // positions >= m are padding and order after every record
+    }
+    if (tid == 0) {
+      atomicAdd((unsigned long long*)&w.ctrl->stats[5], (unsigned long long)m);
+      atomicAdd((unsigned long long*)&w.ctrl->stats[9], 1ull);
+      atomicMax((unsigned long long*)&w.ctrl->stats[8], (unsigned long long)m);
+    }
+    __syncthreads();
+    for (uint32_t k = 2; k <= P; k <<= 1) {
+      for (uint32_t j = k >> 1; j > 0; j >>= 1) {
+        for (uint32_t p = tid; p < P / 2; p += kRT) {
+          const uint32_t i = ((p & ~(j - 1)) << 1) | (p & (j - 1));
+          const uint32_t ixj = i + j;
+          const uint32_t ia = sm.u.s.idx[i], ib = sm.u.s.idx[ixj];
+          bool gt;  // (key, position) of slot i above that of slot i + j
+          if (ia >= m || ib >= m) {
+            gt = ia > ib;
+          } else {
+            const K ka = sm.u.s.keys[ia], kb = sm.u.s.keys[ib];
+            gt = KeyT<K>::lt(kb, ka) || (KeyT<K>::eq(ka, kb) && ia > ib);
+          }
+          if (gt == ((i & k) == 0)) {
+            sm.u.s.idx[i] = (uint16_t)ib;
+            sm.u.s.idx[ixj] = (uint16_t)ia;
+          }
+        }
+        __syncthreads();
+      }
+    }
+    for (uint32_t p = tid; p < m; p += kRT) sm.fpos[sm.u.s.idx[p]] = (uint16_t)p;
+    __syncthreads();  // keys and positions are dead: the region becomes the staging buffer
+    for (uint32_t c = tid; c < m; c += kRT) sm.u.stage[sm.fpos[c]] = load_rec<K, V>(w, it.buf, it.start + c);
+    __syncthreads();
+    for (uint32_t p = tid; p < m; p += kRT) store_out<K, V>(w, it.start + p, sm.u.stage[p]);
+    __syncthreads();
+  }
+}
+
+// ----------------------------------------------------------------------------
+// finish (collect-reduce, histogram; Sec. 3.5).  Refine windows: a shared-
+// memory hash table finds each key's first occurrence (atomicCAS, then
+// atomicMin, as in the semisort_= base case); first occurrences numbered in
+// window order give group ids, and the values (collect-reduce) or ones
+// (histogram) are added per group.  The G distinct (key, sum) pairs are
+// written compacted over the window's own first G slots (its records are no
+// longer needed; the caller's input is never written, a window of it goes to
+// T instead), histogram counts to the same positions of scratch32.  Heavy
+// outputs: collect-reduce adds the per-subarray partial sums of the count
+// pass, a histogram count is the heavy bucket's size.  item_out receives the
+// number of outputs of each item; a scan and a pack kernel then place them.
+// Unsigned wraparound addition is associative and commutative, so the sums do
+// not depend on the order of the atomic adds.
+// ----------------------------------------------------------------------------
+template <class K>
+struct RedSmem {
+  K keys[kRefMax];
+  uint32_t table[2 * kRefMax];
+  unsigned long long acc[kRefMax];
+  uint16_t gid[kRefMax];
+  uint16_t fo[kRefMax];
+  uint32_t scan_tmp[33];
+  unsigned long long red[32];
+};
+
+__device__ __forceinline__ uint32_t compact_buf(uint32_t buf) { return buf == kBufIn ? (uint32_t)kBufT : buf; }
+
+template <class K, class V, int OP>
+__global__ void __launch_bounds__(kRT, 2) k_finish_reduce(Work w) {
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  RedSmem<K>& sm = *reinterpret_cast<RedSmem<K>*>(smem_raw);
+  using Rec = RecT<K, V>;
+  const uint32_t nfin = w.ctrl->nfin;
+  const int tid = threadIdx.x, lane = tid & 31, wid = tid >> 5;
+  const uint32_t c0t = tid * kRR;
+  const uint64_t salt = refine_salt(w.seed);
+  for (uint32_t itx = blockIdx.x; itx < nfin; itx += gridDim.x) {
+    const Item it = w.items[itx];
+    if (it.kind == kItemHeavyOut) {
+      if constexpr (OP == kOpReduce) {
+        const Seg sg = w.segs[it.level][it.aux];
+        const uint64_t* HP = w.hpart[it.level] + sg.cbase + (uint64_t)it.aux2 * sg.ntiles;
+        unsigned long long v = 0;
+        for (uint32_t t = tid; t < sg.ntiles; t += kRT) v += HP[t];
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(kFull, v, o);
+        if (lane == 0) sm.red[wid] = v;
+        __syncthreads();
+        if (tid == 0) {
+          unsigned long long t = 0;
+          for (int i = 0; i < kRT / 32; ++i) t += sm.red[i];
+          w.item_aux[itx] = t;
+        }
+        __syncthreads();
+      }
+      if (tid == 0) w.item_out[itx] = 1;
+      continue;
+    }
+    const uint32_t m = it.len;
+    if (m > (uint32_t)kRefMax) {
+      if (tid == 0) {
+        set_error(w.ctrl, 8);
+        w.item_out[itx] = 0;
+      }
+      continue;
+    }
+    uint32_t ts = 64;
+    while (ts < 2 * m) ts <<= 1;
+    for (uint32_t c = tid; c < m; c += kRT)
+      sm.keys[c] = it.buf == kBufIn ? reinterpret_cast<const K*>(w.in_k)[it.start + c]
+                                    : reinterpret_cast<const Rec*>(buf_ptr(w, it.buf))[it.start + c].k;
+    for (uint32_t i = tid; i < ts; i += kRT) sm.table[i] = kEmpty;
+    __syncthreads();
+    uint32_t slot[kRR];
+#pragma unroll
+    for (int r = 0; r < kRR; ++r) {
+      const uint32_t c = c0t + r;
+      slot[r] = 0;
+      if (c < m) {
+        const K key = sm.keys[c];
+        uint32_t s = (uint32_t)KeyT<K>::hash(key, salt, false) & (ts - 1);
+        while (true) {
+          uint32_t e = sm.table[s];
+          if (e == kEmpty) {
+            e = atomicCAS(&sm.table[s], kEmpty, c);
+            if (e == kEmpty) break;
+          }
+          if (KeyT<K>::eq(sm.keys[e], key)) {
+            atomicMin(&sm.table[s], c);
+            break;
+          }
+          s = (s + 1) & (ts - 1);
+        }
+        slot[r] = s;
+      }
+    }
+    __syncthreads();
+    uint32_t lab[kRR];
+    uint32_t nfirst = 0;
+#pragma unroll
+    for (int r = 0; r < kRR; ++r) {
+      const uint32_t c = c0t + r;
+      lab[r] = c < m ? sm.table[slot[r]] : 0;
+      nfirst += (c < m && lab[r] == c) ? 1u : 0u;
+    }
+    uint32_t G;
+    uint32_t g0 = block_exclusive_scan(nfirst, sm.scan_tmp, &G);
+#pragma unroll
+    for (int r = 0; r < kRR; ++r) {
+      const uint32_t c = c0t + r;
+      if (c < m && lab[r] == c) {
+        sm.gid[c] = (uint16_t)g0;
+        sm.fo[g0] = (uint16_t)c;
+        sm.acc[g0] = 0;
+        ++g0;
+      }
+    }
+    __syncthreads();
+#pragma unroll
+    for (int r = 0; r < kRR; ++r) {
+      const uint32_t c = c0t + r;
+      if (c < m) {
+        unsigned long long v = 1;
+        if constexpr (OP == kOpReduce) {
+          v = it.buf == kBufIn ? reinterpret_cast<const uint64_t*>(w.in_v)[it.start + c]
+                               : (uint64_t)reinterpret_cast<const Rec*>(buf_ptr(w, it.buf))[it.start + c].v;
+        }
+        atomicAdd(&sm.acc[sm.gid[lab[r]]], v);
+      }
+    }
+    __syncthreads();  // every record of the window has been read
+    Rec* cb = reinterpret_cast<Rec*>(buf_ptr(w, compact_buf(it.buf)));
+    for (uint32_t g = tid; g < G; g += kRT) {
+      Rec o;
+      o.k = sm.keys[sm.fo[g]];
+      if constexpr (OP == kOpReduce) o.v = (uint64_t)sm.acc[g];
+      cb[it.start + g] = o;
+      if constexpr (OP == kOpHist) w.scratch32[it.start + g] = (uint32_t)sm.acc[g];
+    }
+    if (tid == 0) {
+      w.item_out[itx] = G;
+      atomicAdd((unsigned long long*)&w.ctrl->stats[5], (unsigned long long)m);
+      atomicAdd((unsigned long long*)&w.ctrl->stats[9], 1ull);
+      atomicMax((unsigned long long*)&w.ctrl->stats[8], (unsigned long long)m);
+      if (G == m) atomicAdd((unsigned long long*)&w.ctrl->stats[10], (unsigned long long)m);
+    }
+    __syncthreads();
+  }
+}
+
+// ----------------------------------------------------------------------------
+// Output placement for collect-reduce / histogram (the packing step of
+// Sec. 3.5): an exclusive scan of item_out in item order (three kernels:
+// chunk totals, one-CTA scan of the totals, chunk-local scans), then a pack
+// kernel that copies each item's outputs to the caller's arrays.  Item order
+// is deterministic, so the output order is too.
+// ----------------------------------------------------------------------------
+constexpr uint32_t kScanChunk = 4096;  // items per CTA (1024 threads x 4)
+
+__global__ void __launch_bounds__(1024) k_iscan_a(Work w) {
+  __shared__ uint64_t tmp[33];
+  const uint32_t nfin = w.ctrl->nfin;
+  const uint64_t c0 = (uint64_t)blockIdx.x * kScanChunk;
+  if (c0 >= nfin) return;
+  uint64_t s = 0;
+#pragma unroll
+  for (int r = 0; r < 4; ++r) {
+    const uint64_t i = c0 + threadIdx.x * 4 + r;
+    if (i < nfin) s += w.item_out[i];
+  }
+  uint64_t tot;
+  block_exclusive_scan64(s, tmp, &tot);
+  if (threadIdx.x == 0) w.block_sums[blockIdx.x] = tot;
+}
+
+__global__ void __launch_bounds__(1024) k_iscan_b(Work w) {
+  __shared__ uint64_t tmp[33];
+  __shared__ uint64_t carry;
+  const uint32_t nfin = w.ctrl->nfin;
+  const uint32_t nch = (nfin + kScanChunk - 1) / kScanChunk;
+  if (threadIdx.x == 0) carry = 0;
+  __syncthreads();
+  for (uint32_t b0 = 0; b0 < nch; b0 += blockDim.x) {
+    const uint32_t b = b0 + threadIdx.x;
+    const uint64_t v = b < nch ? w.block_sums[b] : 0;
+    uint64_t tot;
+    const uint64_t ex = block_exclusive_scan64(v, tmp, &tot);
+    if (b < nch) w.block_sums[b] = carry + ex;
+    __syncthreads();
+    if (threadIdx.x == 0) carry += tot;
+    __syncthreads();
+  }
+  if (threadIdx.x == 0) {
+    *w.num_unique = carry;
+    if (carry > w.out_capacity) set_error(w.ctrl, 4 /*SS_ERR_CAPACITY*/);
+  }
+}
+
+__global__ void __launch_bounds__(1024) k_iscan_c(Work w) {
+  __shared__ uint64_t tmp[33];
+  const uint32_t nfin = w.ctrl->nfin;
+  const uint64_t c0 = (uint64_t)blockIdx.x * kScanChunk;
+  if (c0 >= nfin) return;
+  uint64_t v[4], s = 0;
+#pragma unroll
+  for (int r = 0; r < 4; ++r) {
+    const uint64_t i = c0 + threadIdx.x * 4 + r;
+    v[r] = i < nfin ? w.item_out[i] : 0;
+    s += v[r];
+  }
+  uint64_t tot;
+  uint64_t run = w.block_sums[blockIdx.x] + block_exclusive_scan64(s, tmp, &tot);
+#pragma unroll
+  for (int r = 0; r < 4; ++r) {
+    const uint64_t i = c0 + threadIdx.x * 4 + r;
+    if (i < nfin) w.item_pos[i] = run;
+    run += v[r];
+  }
+}
+
+// One warp per item.  Outputs at positions >= capacity are not written.
+template <class K, class V, int OP>
+__global__ void __launch_bounds__(256) k_pack(Work w) {
+  using Rec = RecT<K, V>;
+  const uint32_t nfin = w.ctrl->nfin;
+  const uint32_t lane = threadIdx.x & 31;
+  const uint32_t gw = (blockIdx.x * blockDim.x + threadIdx.x) >> 5, nwarps = (gridDim.x * blockDim.x) >> 5;
+  K* uk = reinterpret_cast<K*>(w.out_k);
+  const uint64_t cap = w.out_capacity;
+  for (uint32_t itx = gw; itx < nfin; itx += nwarps) {
+    const Item it = w.items[itx];
+    const uint64_t pos = w.item_pos[itx];
+    if (it.kind == kItemHeavyOut) {
+      if (lane == 0 && pos < cap) {
+        const Seg sg = w.segs[it.level][it.aux];
+        uk[pos] = reinterpret_cast<const K*>(w.hkeys[it.level])[sg.bbase + it.aux2];
+        if constexpr (OP == kOpReduce)
+          reinterpret_cast<uint64_t*>(w.sums_out)[pos] = w.item_aux[itx];
+        else
+          reinterpret_cast<uint32_t*>(w.sums_out)[pos] = it.len;
+      }
+      continue;
+    }
+    const uint32_t cnt = (uint32_t)w.item_out[itx];
+    const Rec* cb = reinterpret_cast<const Rec*>(buf_ptr(w, compact_buf(it.buf)));
+    for (uint32_t g = lane; g < cnt; g += 32) {
+      if (pos + g >= cap) break;
+      const Rec r = cb[it.start + g];
+      uk[pos + g] = r.k;
+      if constexpr (OP == kOpReduce)
+        reinterpret_cast<uint64_t*>(w.sums_out)[pos + g] = (uint64_t)r.v;
+      else
+        reinterpret_cast<uint32_t*>(w.sums_out)[pos + g] = w.scratch32[it.start + g];
+    }
   }
 }
 

@@ -50,12 +50,21 @@ cudaError_t launch_pipeline(const Plan& P, const Work& w, cudaStream_t st, const
   PhaseTimer* tm = cfg.timer;
   const int nsm = cfg.num_sms;
   const size_t dist_smem = sizeof(DistSmem<K, V>);
-  const size_t ref_smem = sizeof(RefSmem<K, V>);
+  size_t ref_smem = 0;
   cudaError_t e;
   if ((e = set_smem(k_distribute<K, V, OP>, dist_smem)) != cudaSuccess) return e;
-  if ((e = set_smem(k_finish_equal<K, V>, ref_smem)) != cudaSuccess) return e;
+  if constexpr (OP == kOpEqual) {
+    ref_smem = sizeof(RefSmem<K, V>);
+    if ((e = set_smem(k_finish_equal<K, V>, ref_smem)) != cudaSuccess) return e;
+  } else if constexpr (OP == kOpLess) {
+    ref_smem = sizeof(LessSmem<K, V>);
+    if ((e = set_smem(k_finish_less<K, V>, ref_smem)) != cudaSuccess) return e;
+  } else {
+    ref_smem = sizeof(RedSmem<K>);
+    if ((e = set_smem(k_finish_reduce<K, V, OP>, ref_smem)) != cudaSuccess) return e;
+  }
   const uint32_t s_cap_max = P.s1 > P.s2 ? P.s1 : P.s2;
-  if ((e = set_smem(k_sample<K, V>, (size_t)s_cap_max * sizeof(K))) != cudaSuccess) return e;
+  if ((e = set_smem(k_sample<K, V, OP>, (size_t)s_cap_max * sizeof(K))) != cudaSuccess) return e;
 
   int& nl = *cfg.launches;
   k_init<<<1, 32, 0, st>>>(w);
@@ -67,10 +76,10 @@ cudaError_t launch_pipeline(const Plan& P, const Work& w, cudaStream_t st, const
       const uint32_t segs = P.seg_cap[level];
       const uint32_t tiles = P.tile_cap[level];
       auto cap = [](uint32_t want, uint32_t lim) { return want < lim ? (want ? want : 1) : lim; };
-      k_plan<<<1, 1024, 0, st>>>(w, level);
+      k_plan<OP><<<1, 1024, 0, st>>>(w, level);
       if (tm) tm->mark(level == 0 ? "plan.L0" : "plan.L1+");
       const uint32_t s_cap = level == 0 ? P.s1 : P.s2;
-      k_sample<K, V><<<cap(segs, nsm * 2), 1024, (size_t)s_cap * sizeof(K), st>>>(w, lb, s_cap);
+      k_sample<K, V, OP><<<cap(segs, nsm * 2), 1024, (size_t)s_cap * sizeof(K), st>>>(w, lb, s_cap);
       if (tm) tm->mark(level == 0 ? "sample.L0" : "sample.L1+");
       k_count<K, V, OP><<<cap(tiles, nsm * 4), kCountThreads, 0, st>>>(w, lb);
       if (tm) tm->mark(level == 0 ? "count.L0" : "count.L1+");
@@ -84,10 +93,25 @@ cudaError_t launch_pipeline(const Plan& P, const Work& w, cudaStream_t st, const
       if (tm) tm->mark(level == 0 ? "emit.L0" : "emit.L1+");
     }
   }
-  if (OP == kOpEqual) {
+  if constexpr (OP == kOpEqual) {
     k_finish_equal<K, V><<<nsm * 2, kRT, ref_smem, st>>>(w);
     ++nl;
     if (tm) tm->mark("refine");
+  } else if constexpr (OP == kOpLess) {
+    k_finish_less<K, V><<<nsm * 2, kRT, ref_smem, st>>>(w);
+    ++nl;
+    if (tm) tm->mark("refine");
+  } else {
+    k_finish_reduce<K, V, OP><<<nsm * 2, kRT, ref_smem, st>>>(w);
+    if (tm) tm->mark("refine");
+    const uint32_t nch = (P.item_cap + kScanChunk - 1) / kScanChunk;
+    k_iscan_a<<<nch, 1024, 0, st>>>(w);
+    k_iscan_b<<<1, 1024, 0, st>>>(w);
+    k_iscan_c<<<nch, 1024, 0, st>>>(w);
+    if (tm) tm->mark("scan_out");
+    k_pack<K, V, OP><<<nsm * 8, 256, 0, st>>>(w);
+    if (tm) tm->mark("pack");
+    nl += 5;
   }
   return cudaGetLastError();
 }

@@ -31,16 +31,16 @@ struct Seg {
   uint32_t len;        // records
   uint32_t ntiles;     // subarrays
   uint32_t first_tile; // index of the first subarray in the level's tile list
-  uint32_t bbase;      // base of the segment's bucket rows / heavy table (capacity 2 n_L)
+  uint32_t bbase;      // base of the segment's bucket rows / heavy table (capacity nbcap)
   uint64_t cbase;      // base of the segment's count matrix (nbcap x ntiles, bucket-major)
   uint32_t lbits;      // log2 n_L
-  uint32_t nh;         // heavy keys found by sampling
-  uint32_t nbcap;      // n_L + heavy capacity
+  uint32_t nh;         // heavy keys found by sampling (semisort_<: splitter boundaries)
+  uint32_t nbcap;      // bucket-id capacity of the segment
   uint32_t fin_off;    // first finish item emitted by this segment
   uint32_t next_off;   // first next-level segment emitted by this segment
   uint32_t cnt_fin;    // finish items emitted
   uint32_t cnt_next;   // next-level segments emitted
-  uint32_t pad;
+  uint32_t nb;         // bucket ids in use
   uint64_t mult;       // odd multiplier of this segment's bucketing hash
 };
 
@@ -114,6 +114,9 @@ struct Work {
   uint64_t* num_unique; // user pointer (collect-reduce / histogram)
   void* sums_out;       // user pointer: u64 sums or u32 counts
   void* splitters[kMaxLevels];  // semisort_<: per-segment sorted boundaries at bbase
+  uint32_t* scratch32;  // histogram: per-position counts of compacted base cases
+  uint64_t* item_aux;   // collect-reduce: heavy totals per item
+  uint64_t out_capacity;
   Ctrl* ctrl;
 };
 
@@ -129,7 +132,7 @@ struct Plan {
   size_t off_segs[kMaxLevels], off_tiles[kMaxLevels], off_C[kMaxLevels], off_hkeys[kMaxLevels],
       off_htab[kMaxLevels], off_bsize[kMaxLevels], off_boff[kMaxLevels], off_hpart[kMaxLevels],
       off_split[kMaxLevels];
-  size_t off_items, off_item_out, off_item_pos, off_block_sums, off_ctrl;
+  size_t off_items, off_item_out, off_item_pos, off_block_sums, off_ctrl, off_scratch32, off_item_aux;
   size_t total;
 };
 
