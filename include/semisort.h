@@ -112,8 +112,9 @@ ss_status semisort_less(ss_type key_type, ss_type val_type, const void* keys, co
 /* collect-reduce (Sec. 2.1, Sec. 3.5) with the map M(r) = value and the monoid
  * (+ mod 2^64, 0).  Writes one (unique key, sum) pair per distinct key into
  * ukeys_out/sums_out (capacity entries each) and the number of distinct keys
- * into *d_num_unique (device pointer).  If that number exceeds capacity only
- * the count is written and the device flag SS_ERR_CAPACITY is raised.  Output
+ * into *d_num_unique (device pointer).  If that number exceeds capacity, the
+ * count is still written, only the first `capacity` outputs are stored and the
+ * device flag SS_ERR_CAPACITY is raised.  Output
  * order is unspecified but fixed for a given seed. */
 ss_status collect_reduce(ss_type key_type, const void* keys, const uint64_t* vals, void* ukeys_out,
                          uint64_t* sums_out, uint64_t capacity, uint64_t* d_num_unique, uint64_t n,
@@ -123,6 +124,32 @@ ss_status collect_reduce(ss_type key_type, const void* keys, const uint64_t* val
 ss_status histogram(ss_type key_type, const void* keys, void* ukeys_out, uint32_t* counts_out,
                     uint64_t capacity, uint64_t* d_num_unique, uint64_t n, void* ws,
                     size_t ws_bytes, const ss_options* opt, ss_stream_t stream);
+
+/* semisort_= without a workspace argument and without allocating anything.
+ * The paper has no counterpart: this entry point exists for callers that must
+ * not allocate device memory at the time of the call and have no workspace to
+ * hand over -- for instance code running under a fixed device-memory budget
+ * that another framework's caching allocator has already taken, or a loop that
+ * cannot afford the device-wide synchronization cudaMalloc may cause.
+ * Scratch space is one static device array of 24 MiB inside the library,
+ * shared by every call on a device; it keeps whatever the last call left in it.
+ * Limits and behaviour:
+ *  - n <= 262144 (2^18) records; larger n returns SS_ERR_UNSUPPORTED.  Options
+ *    whose plan would not fit the array (ss_workspace_size() above 24 MiB)
+ *    return SS_ERR_WORKSPACE_TOO_SMALL.
+ *  - The first call on each device looks up the array's device address
+ *    (cudaGetSymbolAddress) and remembers it; make that first call before any
+ *    stream capture begins.
+ *  - Calls that may overlap in time (different streams or host threads without
+ *    ordering between them) race on the shared array and give wrong results;
+ *    order them on one stream or synchronize between them.
+ *  - SS_FLAG_PHASE_TIMING is ignored.  A device-side failure (the recursion
+ *    depth limit) sets the flag inside the internal array, where callers cannot
+ *    read it.
+ * Other arguments, output and errors as semisort_equal. */
+ss_status semisort_equal_noalloc(ss_type key_type, ss_type val_type, const void* keys,
+                                 const void* vals, void* keys_out, void* vals_out, uint64_t n,
+                                 const ss_options* opt, ss_stream_t stream);
 
 /* Reads (and clears) the device error flag left in `ws` by earlier calls on
  * `stream`; synchronizes the stream.  *code receives the ss_status of the

@@ -68,6 +68,8 @@ def lib():
                 f = getattr(L, name)
                 f.argtypes = [i32, i32, vp, vp, vp, vp, u64, vp, sz, vp, vp]
                 f.restype = i32
+            L.semisort_equal_noalloc.argtypes = [i32, i32, vp, vp, vp, vp, u64, vp, vp]
+            L.semisort_equal_noalloc.restype = i32
             L.collect_reduce.argtypes = [i32, vp, vp, vp, vp, u64, vp, u64, vp, sz, vp, vp]
             L.collect_reduce.restype = i32
             L.histogram.argtypes = [i32, vp, vp, vp, u64, vp, u64, vp, sz, vp, vp]
@@ -168,6 +170,15 @@ def _semisort(fn, op, keys, vals, keys_out, vals_out, workspace, options, stream
 def semisort_equal(keys, vals=None, keys_out=None, vals_out=None, workspace=None, options=None, stream=None):
     """semisort_=: records with equal keys become contiguous, stable."""
     return _semisort(lib().semisort_equal, OP_EQUAL, keys, vals, keys_out, vals_out, workspace, options, stream)
+
+
+def semisort_equal_noalloc(keys, vals, keys_out, vals_out, options=None, stream=None):
+    """semisort_= on at most 2^18 records with the library's static scratch
+    array (no workspace, nothing allocated); outputs are caller tensors."""
+    code = lib().semisort_equal_noalloc(key_code(keys), val_code(vals), _ptr(keys), _ptr(vals), _ptr(keys_out),
+                                        _ptr(vals_out), keys.shape[0], _opt_ptr(options), _stream(stream))
+    _check(code, "semisort_equal_noalloc")
+    return keys_out, vals_out
 
 
 def semisort_less(keys, vals=None, keys_out=None, vals_out=None, workspace=None, options=None, stream=None):

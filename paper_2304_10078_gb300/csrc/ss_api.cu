@@ -436,3 +436,53 @@ ss_status ss_hash_u64(const uint64_t* keys, uint64_t* out, uint64_t n, uint64_t 
 }
 
 }  // extern "C"
+
+// ---------------------------------------------------------------------------
+// semisort_equal_noalloc: semisort_= whose scratch space is a file-scope
+// device array of this translation unit instead of a caller workspace.
+// ---------------------------------------------------------------------------
+namespace {
+
+constexpr uint64_t kNoAllocMaxN = 1ull << 18;      // records per call
+constexpr size_t kNoAllocBytes = 24ull << 20;      // covers every plan up to kNoAllocMaxN with alpha >= 64
+
+static __device__ __align__(256) unsigned char g_noalloc_ws[kNoAllocBytes];
+
+std::mutex g_noalloc_mu;
+void* g_noalloc_ptr[64] = {};
+
+// Device address of the array on the current device, looked up once per device.
+ss_status noalloc_workspace(void** out) {
+  int dev = 0;
+  if (cudaGetDevice(&dev) != cudaSuccess) return SS_ERR_CUDA;
+  if (dev < 0 || dev >= 64) return SS_ERR_UNSUPPORTED;
+  std::lock_guard<std::mutex> g(g_noalloc_mu);
+  if (!g_noalloc_ptr[dev]) {
+    void* p = nullptr;
+    if (cudaGetSymbolAddress(&p, g_noalloc_ws) != cudaSuccess || p == nullptr) return SS_ERR_CUDA;
+    g_noalloc_ptr[dev] = p;
+  }
+  *out = g_noalloc_ptr[dev];
+  return SS_OK;
+}
+
+}  // namespace
+
+extern "C" ss_status semisort_equal_noalloc(ss_type key_type, ss_type val_type, const void* keys, const void* vals,
+                                            void* keys_out, void* vals_out, uint64_t n, const ss_options* opt,
+                                            ss_stream_t stream) {
+  if (n > kNoAllocMaxN) return SS_ERR_UNSUPPORTED;
+  if (n == 0) return SS_OK;
+  void* ws = nullptr;
+  const ss_status s = noalloc_workspace(&ws);
+  if (s != SS_OK) return s;
+  // Phase timing creates CUDA events, so this entry point ignores that flag.
+  ss_options o;
+  memset(&o, 0, sizeof(o));
+  if (opt) o = *opt;
+  o.flags &= ~SS_FLAG_PHASE_TIMING;
+  // Nothing in the array has to start at zero: the pipeline's first kernel
+  // resets the control block, and every other region is written before it is read.
+  return semisort_common(kOpEqual, key_type, val_type, keys, vals, keys_out, vals_out, n, ws, kNoAllocBytes, &o,
+                         stream);
+}
