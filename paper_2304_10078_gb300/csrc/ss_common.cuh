@@ -240,15 +240,35 @@ __device__ __forceinline__ int bpad(int q) { return q + (q >> 5); }
 // Records of the temporary arrays (array of structures, so a record is one
 // contiguous access); V = void means keys only.
 // ---------------------------------------------------------------------------
+// Alignment of a record: the largest power of two (up to 16) that its size
+// allows, so that one record moves with one vector load or store.
 template <class K, class V>
-struct RecT {
+struct RecAlign {
+  static constexpr size_t bytes = sizeof(K) + sizeof(V);
+  static constexpr size_t value = bytes > 8 ? 16 : (bytes > 4 ? 8 : 4);
+};
+template <class K, class V>
+struct alignas(RecAlign<K, V>::value) RecT {
   K k;
   V v;
 };
 template <class K>
-struct RecT<K, void> {
+struct alignas(sizeof(K) >= 16 ? 16 : sizeof(K)) RecT<K, void> {
   K k;
 };
+
+// Slot of record i in a shared-memory staging buffer of RB-byte records.  An
+// XOR swizzle inside every 128-byte row keeps both access patterns of the
+// kernels free of bank conflicts: consecutive i (coalesced copies) and
+// i = 16 t + r for t = 0..31 (thread t holding 16 consecutive records).
+template <int RB>
+__device__ __forceinline__ uint32_t sw(uint32_t i) {
+  constexpr uint32_t L = RB >= 128 ? 1u : 128u / RB;  // records per 128-byte row
+  if constexpr (L <= 1)
+    return i;
+  else
+    return (i & ~(L - 1)) | ((i ^ (i >> 4)) & (L - 1));
+}
 
 template <class V>
 struct ValT {

@@ -611,10 +611,12 @@ __global__ void __launch_bounds__(1024) k_scan(Work w, LevelBufs lb) {
 
 // ----------------------------------------------------------------------------
 // distribute: the second pass of Blocked Distributing (Sec. 3.2).  Each CTA
-// walks its subarray chunk by chunk in input order.  Inside a chunk the
-// records are ranked stably by bucket id (BlockRank, two 5-bit passes, no
-// atomics), staged in shared memory in bucket order, and written as
-// contiguous runs at X[bucket][subarray] + (records of that bucket already
+// walks its subarray chunk by chunk in input order.  A chunk of records is
+// copied once, coalesced, into a swizzled shared buffer; every thread then
+// takes 16 consecutive records from it, computes their buckets and ranks them
+// stably by bucket id (BlockRank, two 5-bit passes, no atomics).  The output
+// pass walks the chunk in rank order, so each bucket's records leave as one
+// contiguous run at X[bucket][subarray] + (records of that bucket already
 // written): stable, and no two CTAs ever write the same slot (race-free).
 // Light records go to the level's temporary array (records), heavy records
 // straight to their final place.
@@ -626,26 +628,54 @@ using DRank = BlockRank<kDT, kDR, 5>;
 
 template <class K, class V>
 struct DistSmem {
-  union {
-    struct {
-      typename DRank::Smem rk;
-      uint32_t tmp[kDCH + kDCH / 32];
-    } a;
-    RecT<K, V> stage[kDCH];
-  } u;
-  uint16_t fpos[kDCH];
-  uint16_t sbid[kDCH];
-  uint32_t running[kMaxBuckets];
-  uint32_t base[kMaxBuckets];
+  RecT<K, V> S[kDCH];                // the chunk, swizzled (sw)
+  typename DRank::Smem rk;
+  uint32_t px[kDCH + kDCH / 32];     // (bucket << 16 | chunk index) at rank, padded (bpad)
+  uint32_t cur[kMaxBuckets];         // next write offset per bucket within the segment
   K hk[kMaxHeavy];
   uint16_t ht[4 * kMaxHeavy];
 };
+
+// Record i of a level's source (caller SoA at level 0, AoS records after).
+template <class K, class V>
+__device__ __forceinline__ RecT<K, V> read_src(const LevelBufs& lb, uint64_t i) {
+  RecT<K, V> r;
+  if (lb.src_aos) {
+    r = reinterpret_cast<const RecT<K, V>*>(lb.src_k)[i];
+  } else {
+    r.k = reinterpret_cast<const K*>(lb.src_k)[i];
+    if constexpr (!std::is_same<V, void>::value) r.v = reinterpret_cast<const V*>(lb.src_v)[i];
+  }
+  return r;
+}
+
+// Coalesced copy of `len` records starting at global index g into S; eight
+// independent loads per thread are in flight before the first store.
+template <int NT, class K, class V, class Src>
+__device__ __forceinline__ void load_chunk(RecT<K, V>* S, uint32_t len, Src src) {
+  using Rec = RecT<K, V>;
+  constexpr int B = 8;
+  for (uint32_t i0 = 0; i0 < len; i0 += B * NT) {
+    Rec t[B];
+#pragma unroll
+    for (int u = 0; u < B; ++u) {
+      const uint32_t i = i0 + u * NT + threadIdx.x;
+      if (i < len) t[u] = src(i);
+    }
+#pragma unroll
+    for (int u = 0; u < B; ++u) {
+      const uint32_t i = i0 + u * NT + threadIdx.x;
+      if (i < len) S[sw<sizeof(Rec)>(i)] = t[u];
+    }
+  }
+}
 
 template <class K, class V, int OP>
 __global__ void __launch_bounds__(kDT, 2) k_distribute(Work w, LevelBufs lb) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
   DistSmem<K, V>& sm = *reinterpret_cast<DistSmem<K, V>*>(smem_raw);
   using Rec = RecT<K, V>;
+  constexpr int RB = sizeof(Rec);
   constexpr bool kVals = !std::is_same<V, void>::value;
   using VV = typename ValT<V>::type;
   const uint32_t nt = w.ctrl->ntiles[lb.level];
@@ -663,73 +693,45 @@ __global__ void __launch_bounds__(kDT, 2) k_distribute(Work w, LevelBufs lb) {
     {
       const uint32_t* X = w.C[lb.level] + sg.cbase;
       const uint32_t* boff = w.boff[lb.level] + sg.bbase;
-      for (uint32_t b = tid; b < nb; b += kDT) sm.running[b] = boff[b] + X[(uint64_t)b * sg.ntiles + tl.idx];
+      for (uint32_t b = tid; b < nb; b += kDT) sm.cur[b] = boff[b] + X[(uint64_t)b * sg.ntiles + tl.idx];
     }
-    __syncthreads();
     const bool two_pass = nb > 32;
     for (uint32_t c0 = 0; c0 < tl.len; c0 += kDCH) {
       const uint32_t clen = tl.len - c0 < (uint32_t)kDCH ? tl.len - c0 : (uint32_t)kDCH;
       const uint64_t gbase = tl.start + c0;
+      load_chunk<kDT, K, V>(sm.S, clen, [&](uint32_t i) { return read_src<K, V>(lb, gbase + i); });
+      __syncthreads();
       uint32_t bid[kDR], rk[kDR];
-      {
-        K key[kDR];
+      // invalid slots get the largest bucket id: both 5-bit digits are 31, and
+      // as the last items in blocked order they rank after every valid record
 #pragma unroll
-        for (int r = 0; r < kDR; ++r)
-          if (c0t + r < clen) key[r] = load_key<K, V>(lb.src_k, lb.src_aos, gbase + c0t + r);
-        // invalid slots get the largest bucket id: both 5-bit digits are 31, so they rank last
+      for (int r = 0; r < kDR; ++r)
+        bid[r] = c0t + r < clen ? bucket_in<K, OP>(sm.S[sw<RB>(c0t + r)].k, sg, sm.hk, sm.ht, tmask)
+                                : (kMaxBuckets - 1);
+      DRank::rank(sm.rk, bid, 0, rk);
 #pragma unroll
-        for (int r = 0; r < kDR; ++r)
-          bid[r] = c0t + r < clen ? bucket_in<K, OP>(key[r], sg, sm.hk, sm.ht, tmask)
-                                  : (kMaxBuckets - 1);
-      }
-      DRank::rank(sm.u.a.rk, bid, 0, rk);
-      if (!two_pass) {
-#pragma unroll
-        for (int r = 0; r < kDR; ++r) {
-          sm.fpos[c0t + r] = (uint16_t)rk[r];
-          sm.sbid[rk[r]] = (uint16_t)bid[r];
-        }
-      } else {
-#pragma unroll
-        for (int r = 0; r < kDR; ++r) sm.u.a.tmp[bpad(rk[r])] = (bid[r] << 16) | (c0t + r);
+      for (int r = 0; r < kDR; ++r) sm.px[bpad(rk[r])] = (bid[r] << 16) | (c0t + r);
+      if (two_pass) {
         __syncthreads();
         uint32_t x[kDR];
 #pragma unroll
-        for (int r = 0; r < kDR; ++r) x[r] = sm.u.a.tmp[bpad(c0t + r)];
-        DRank::rank(sm.u.a.rk, x, 21, rk);
+        for (int r = 0; r < kDR; ++r) x[r] = sm.px[bpad(c0t + r)];
+        DRank::rank(sm.rk, x, 21, rk);
 #pragma unroll
-        for (int r = 0; r < kDR; ++r) {
-          sm.fpos[x[r] & 0xFFFFu] = (uint16_t)rk[r];
-          sm.sbid[rk[r]] = (uint16_t)(x[r] >> 16);
-        }
+        for (int r = 0; r < kDR; ++r) sm.px[bpad(rk[r])] = x[r];
       }
       __syncthreads();
-      // stage records in bucket order (the rank scratch is dead now); the
-      // records are read again (cache hits) rather than held in registers
-#pragma unroll
-      for (int r = 0; r < kDR; ++r) {
-        const uint32_t c = c0t + r;
-        if (c < clen) {
-          Rec rec;
-          if (lb.src_aos) {
-            rec = reinterpret_cast<const Rec*>(lb.src_k)[gbase + c];
-          } else {
-            rec.k = reinterpret_cast<const K*>(lb.src_k)[gbase + c];
-            if constexpr (kVals) rec.v = reinterpret_cast<const VV*>(lb.src_v)[gbase + c];
-          }
-          sm.u.stage[sm.fpos[c]] = rec;
-        }
-      }
+      // run starts: turn the bucket's running offset into the base of this chunk
       for (uint32_t p = tid; p < clen; p += kDT) {
-        const uint32_t b = sm.sbid[p];
-        if (p == 0 || sm.sbid[p - 1] != b) sm.base[b] = sm.running[b] - p;
+        const uint32_t b = sm.px[bpad(p)] >> 16;
+        if (p == 0 || (sm.px[bpad(p - 1)] >> 16) != b) sm.cur[b] -= p;
       }
       __syncthreads();
       for (uint32_t p = tid; p < clen; p += kDT) {
-        const uint32_t b = sm.sbid[p];
-        const uint32_t rel = sm.base[b] + p;
-        const uint64_t pos = sg.start + rel;
-        const Rec rec = sm.u.stage[p];
+        const uint32_t x = sm.px[bpad(p)];
+        const uint32_t b = x >> 16;
+        const uint64_t pos = sg.start + sm.cur[b] + p;
+        const Rec rec = sm.S[sw<RB>(x & 0xFFFFu)];
         if (!is_heavy<OP>(b, nl)) {
           dst[pos] = rec;
         } else if constexpr (kMoveHeavy) {
@@ -740,7 +742,12 @@ __global__ void __launch_bounds__(kDT, 2) k_distribute(Work w, LevelBufs lb) {
             if constexpr (kVals) reinterpret_cast<VV*>(lb.hdst_v)[pos] = rec.v;
           }
         }
-        if (p == clen - 1 || sm.sbid[p + 1] != b) sm.running[b] = rel + 1;
+      }
+      __syncthreads();
+      // run ends: the next chunk continues after this chunk's run
+      for (uint32_t p = tid; p < clen; p += kDT) {
+        const uint32_t b = sm.px[bpad(p)] >> 16;
+        if (p + 1 == clen || (sm.px[bpad(p + 1)] >> 16) != b) sm.cur[b] += p + 1;
       }
       __syncthreads();
     }
@@ -880,13 +887,15 @@ __global__ void __launch_bounds__(1024) k_emit(Work w, LevelBufs lb) {
 // most alpha records, and the copy-back of Sec. 3.4 for heavy buckets left in
 // the temporary array.
 //
-// Base case: a shared-memory hash table maps each key to the index of its
-// first occurrence in the bucket (insert by atomicCAS, then atomicMin, so the
+// Base case: the window's records are copied once, coalesced, into a swizzled
+// shared buffer.  A shared-memory hash table maps each key to the index of its
+// first occurrence in the window (insert by atomicCAS, then atomicMin, so the
 // label does not depend on scheduling).  A scan over first occurrences turns
 // labels into group ids 0..G-1 in first-occurrence order; ranking the records
 // stably by group id (BlockRank, ceil(log2 G)/5 passes) puts every group in one
 // run, groups in first-occurrence order and records of a group in input order
-// -- the same result as the chained hash table of Sec. 3.3.
+// -- the same result as the chained hash table of Sec. 3.3.  The output is
+// written in rank order, coalesced, from the shared buffer.
 // ----------------------------------------------------------------------------
 constexpr int kRT = 256;
 constexpr int kRR = 16;
@@ -895,19 +904,12 @@ using RRank = BlockRank<kRT, kRR, 5>;
 
 template <class K, class V>
 struct RefSmem {
+  RecT<K, V> S[kRefMax];  // the window, swizzled (sw)
   union {
-    struct {
-      K keys[kRefMax];
-      uint32_t table[2 * kRefMax];
-    } h;
-    struct {
-      typename RRank::Smem rk;
-      uint32_t tmp[kRefMax + kRefMax / 32];
-    } a;
-    RecT<K, V> stage[kRefMax];
+    uint32_t table[2 * kRefMax];
+    typename RRank::Smem rk;
   } u;
-  uint16_t fpos[kRefMax];
-  uint16_t gid[kRefMax];
+  uint32_t px[kRefMax + kRefMax / 32];  // group id by first occurrence; then (group << 16 | index) at rank
   uint32_t scan_tmp[33];
 };
 
@@ -930,10 +932,32 @@ __device__ __forceinline__ void store_out(const Work& w, uint64_t pos, const Rec
   if constexpr (!std::is_same<V, void>::value) reinterpret_cast<V*>(w.out_v)[pos] = r.v;
 }
 
+// Copy-back of Sec. 3.4: records of an item from the temporary array to the
+// output, eight independent loads per thread in flight.
+template <int NT, class K, class V>
+__device__ __forceinline__ void copy_item(const Work& w, const Item& it) {
+  constexpr int B = 8;
+  for (uint32_t i0 = 0; i0 < it.len; i0 += B * NT) {
+    RecT<K, V> t[B];
+#pragma unroll
+    for (int u = 0; u < B; ++u) {
+      const uint32_t i = i0 + u * NT + threadIdx.x;
+      if (i < it.len) t[u] = load_rec<K, V>(w, it.buf, it.start + i);
+    }
+#pragma unroll
+    for (int u = 0; u < B; ++u) {
+      const uint32_t i = i0 + u * NT + threadIdx.x;
+      if (i < it.len) store_out<K, V>(w, it.start + i, t[u]);
+    }
+  }
+}
+
 template <class K, class V>
 __global__ void __launch_bounds__(kRT, 2) k_finish_equal(Work w) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
   RefSmem<K, V>& sm = *reinterpret_cast<RefSmem<K, V>*>(smem_raw);
+  using Rec = RecT<K, V>;
+  constexpr int RB = sizeof(Rec);
   const uint32_t nfin = w.ctrl->nfin;
   const int tid = threadIdx.x;
   const uint32_t c0t = tid * kRR;
@@ -941,8 +965,7 @@ __global__ void __launch_bounds__(kRT, 2) k_finish_equal(Work w) {
   for (uint32_t itx = blockIdx.x; itx < nfin; itx += gridDim.x) {
     const Item it = w.items[itx];
     if (it.kind == kItemCopy) {
-      for (uint32_t i = tid; i < it.len; i += kRT)
-        store_out<K, V>(w, it.start + i, load_rec<K, V>(w, it.buf, it.start + i));
+      copy_item<kRT, K, V>(w, it);
       if (tid == 0) atomicAdd((unsigned long long*)&w.ctrl->stats[6], (unsigned long long)it.len);
       continue;
     }
@@ -953,104 +976,92 @@ __global__ void __launch_bounds__(kRT, 2) k_finish_equal(Work w) {
     }
     uint32_t ts = 64;
     while (ts < 2 * m) ts <<= 1;
-    uint32_t slot[kRR];
-    for (uint32_t c = tid; c < m; c += kRT)
-      sm.u.h.keys[c] = it.buf == kBufIn ? reinterpret_cast<const K*>(w.in_k)[it.start + c]
-                                        : reinterpret_cast<const RecT<K, V>*>(buf_ptr(w, it.buf))[it.start + c].k;
-    for (uint32_t i = tid; i < ts; i += kRT) sm.u.h.table[i] = kEmpty;
+    load_chunk<kRT, K, V>(sm.S, m, [&](uint32_t i) { return load_rec<K, V>(w, it.buf, it.start + i); });
+    for (uint32_t i = tid; i < ts; i += kRT) sm.u.table[i] = kEmpty;
     __syncthreads();
+    uint32_t slot2[kRR / 2];  // two 16-bit table slots per word
 #pragma unroll
     for (int r = 0; r < kRR; ++r) {
       const uint32_t c = c0t + r;
-      slot[r] = 0;
+      uint32_t s = 0;
       if (c < m) {
-        const K key = sm.u.h.keys[c];
+        const K key = sm.S[sw<RB>(c)].k;
         const uint64_t h = KeyT<K>::hash(key, salt, false);
-        uint32_t s = (uint32_t)h & (ts - 1);
+        s = (uint32_t)h & (ts - 1);
         while (true) {
-          uint32_t e = sm.u.h.table[s];
+          uint32_t e = sm.u.table[s];
           if (e == kEmpty) {
-            e = atomicCAS(&sm.u.h.table[s], kEmpty, c);
+            e = atomicCAS(&sm.u.table[s], kEmpty, c);
             if (e == kEmpty) break;
           }
-          if (KeyT<K>::eq(sm.u.h.keys[e], key)) {
-            atomicMin(&sm.u.h.table[s], c);
+          if (KeyT<K>::eq(sm.S[sw<RB>(e)].k, key)) {
+            atomicMin(&sm.u.table[s], c);
             break;
           }
           s = (s + 1) & (ts - 1);
         }
-        slot[r] = s;
       }
+      if (r & 1)
+        slot2[r >> 1] |= s << 16;
+      else
+        slot2[r >> 1] = s;
     }
     __syncthreads();
-    // first-occurrence labels -> group ids in first-occurrence order
-    uint32_t lab[kRR];
+    // first-occurrence labels (kept per record in px) -> group ids in
+    // first-occurrence order (kept per first occurrence in the table region)
     uint32_t nfirst = 0;
 #pragma unroll
     for (int r = 0; r < kRR; ++r) {
       const uint32_t c = c0t + r;
-      lab[r] = c < m ? sm.u.h.table[slot[r]] : 0;
-      nfirst += (c < m && lab[r] == c) ? 1u : 0u;
+      const uint32_t lab = c < m ? sm.u.table[(slot2[r >> 1] >> ((r & 1) * 16)) & 0xFFFFu] : 0;
+      sm.px[bpad(c)] = lab;
+      nfirst += (c < m && lab == c) ? 1u : 0u;
     }
     uint32_t G;
-    uint32_t g0 = block_exclusive_scan(nfirst, sm.scan_tmp, &G);
-#pragma unroll
-    for (int r = 0; r < kRR; ++r) {
-      const uint32_t c = c0t + r;
-      if (c < m && lab[r] == c) sm.gid[c] = (uint16_t)g0++;
-    }
-    __syncthreads();
+    uint32_t g0 = block_exclusive_scan(nfirst, sm.scan_tmp, &G);  // its barriers end the table reads
     if (tid == 0) {
       atomicAdd((unsigned long long*)&w.ctrl->stats[5], (unsigned long long)m);
       atomicAdd((unsigned long long*)&w.ctrl->stats[9], 1ull);
       atomicMax((unsigned long long*)&w.ctrl->stats[8], (unsigned long long)m);
     }
     if (G == m) {
-      // every key distinct: the bucket is already semisorted
+      // every key distinct: the window is already semisorted
       if (tid == 0) atomicAdd((unsigned long long*)&w.ctrl->stats[10], (unsigned long long)m);
-      for (uint32_t c = tid; c < m; c += kRT) store_out<K, V>(w, it.start + c, load_rec<K, V>(w, it.buf, it.start + c));
+      for (uint32_t p = tid; p < m; p += kRT) store_out<K, V>(w, it.start + p, sm.S[sw<RB>(p)]);
       __syncthreads();
       continue;
     }
-    // stable LSD ranking by group id, 5 bits per pass
-    uint32_t g[kRR], rk[kRR], orig[kRR];
-#pragma unroll
-    for (int r = 0; r < kRR; ++r) {
-      g[r] = c0t + r < m ? sm.gid[lab[r]] : 0xFFFu;
-      orig[r] = c0t + r;
-    }
-    const uint32_t gbits = ceil_log2_u32(G) < 1 ? 1 : ceil_log2_u32(G);
-    const uint32_t passes = (gbits + 4) / 5;
-    __syncthreads();  // the hash table region becomes rank scratch
-    for (uint32_t pz = 0; pz < passes; ++pz) {
-      RRank::rank(sm.u.a.rk, g, 5 * pz, rk);
-      if (pz + 1 < passes) {
-#pragma unroll
-        for (int r = 0; r < kRR; ++r) sm.u.a.tmp[bpad(rk[r])] = (g[r] << 16) | orig[r];
-        __syncthreads();
-#pragma unroll
-        for (int r = 0; r < kRR; ++r) {
-          const uint32_t x = sm.u.a.tmp[bpad(c0t + r)];
-          g[r] = x >> 16;
-          orig[r] = x & 0xFFFFu;
-        }
-      }
-    }
-#pragma unroll
-    for (int r = 0; r < kRR; ++r)
-      if (orig[r] < m) sm.fpos[orig[r]] = (uint16_t)rk[r];
-    __syncthreads();
 #pragma unroll
     for (int r = 0; r < kRR; ++r) {
       const uint32_t c = c0t + r;
-      if (c < m) sm.u.stage[sm.fpos[c]] = load_rec<K, V>(w, it.buf, it.start + c);
+      if (c < m && sm.px[bpad(c)] == c) sm.u.table[c] = g0++;
     }
     __syncthreads();
-    for (uint32_t p = tid; p < m; p += kRT) store_out<K, V>(w, it.start + p, sm.u.stage[p]);
+    // stable LSD ranking by group id, 5 bits per pass; padding items get
+    // group 0xFFF and, last in blocked order, rank after every record
+    uint32_t g[kRR], rk[kRR];
+#pragma unroll
+    for (int r = 0; r < kRR; ++r) {
+      const uint32_t c = c0t + r;
+      g[r] = ((c < m ? sm.u.table[sm.px[bpad(c)]] : 0xFFFu) << 16) | c;
+    }
+    const uint32_t gbits = ceil_log2_u32(G) < 1 ? 1 : ceil_log2_u32(G);
+    const uint32_t passes = (gbits + 4) / 5;
+    __syncthreads();  // group ids read: px and the hash table region are free
+    for (uint32_t pz = 0; pz < passes; ++pz) {
+      RRank::rank(sm.u.rk, g, 16 + 5 * pz, rk);
+#pragma unroll
+      for (int r = 0; r < kRR; ++r) sm.px[bpad(rk[r])] = g[r];
+      __syncthreads();
+      if (pz + 1 < passes) {
+#pragma unroll
+        for (int r = 0; r < kRR; ++r) g[r] = sm.px[bpad(c0t + r)];
+      }
+    }
+    for (uint32_t p = tid; p < m; p += kRT) store_out<K, V>(w, it.start + p, sm.S[sw<RB>(sm.px[bpad(p)] & 0xFFFFu)]);
     __syncthreads();
   }
 }
-
 
 // ----------------------------------------------------------------------------
 // finish (semisort_<): the base case of Sec. 3.3 with a comparison sort, and
