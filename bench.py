@@ -155,6 +155,25 @@ def alg_bytes(st: dict) -> int:
     return 40 * dist + 32 * st.get("refined", 0) + 32 * st.get("copied", 0)
 
 
+def dram_traffic_per_launch(n):
+    """DRAM bytes (read + write) of one distribute.L0 launch on n records,
+    from the committed ncu counters scaled by records; None when the kernel
+    sources changed after the counters were taken."""
+    import hashlib
+    try:
+        with open(os.path.join(ROOT, "profiles", "traffic.json")) as f:
+            t = json.load(f)["distribute.L0"]
+        h = hashlib.sha256()
+        for p in t["kernel_sources"]:
+            with open(os.path.join(ROOT, p), "rb") as f:
+                h.update(f.read())
+        if h.hexdigest() != t["kernel_sources_sha256"]:
+            return None
+        return t["bytes_per_record"] * n
+    except (OSError, KeyError, ValueError):
+        return None
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -255,12 +274,7 @@ def main():
     dom_avg = sum(dom_ms) / len(dom_ms) if dom_ms else float("nan")
     dom_b = sum(dom_bytes) / len(dom_bytes)
     achieved = dom_b / (dom_avg / 1000.0) / 1e9 if dom_ms else None
-    traffic = None
-    try:
-        with open(os.path.join(ROOT, "profiles", "traffic.json")) as f:
-            traffic = json.load(f).get("distribute.L0")
-    except Exception:
-        pass
+    traffic = dram_traffic_per_launch(n)
 
     # end to end: pinned host input -> device, the call, result -> pinned host
     e2e = None
@@ -304,7 +318,7 @@ def main():
         "config": {"workload": f"semisort_equal n={n} (u64 key, u64 value=index), steps cycle over "
                                + ", ".join(dist_name(d) for d in dists),
                    "parallelism": "replicas" if world > 1 else "single GPU",
-                   "l2": "inputs (16 GB per step) larger than L2; no flush"},
+                   "l2": f"inputs ({16 * n / 1e9:.3g} GB per step) larger than L2; no flush"},
         "roofline": {"bound": "hbm", "kernel": "distribute.L0",
                      "achieved": achieved, "peak": peak, "peak_kind": peak_kind, "unit": "GB/s",
                      "frac": (achieved / peak) if achieved else None, "traffic": traffic,

@@ -222,7 +222,9 @@ cudaError_t dispatch(int op, int kt, int vt, const Plan& P, const Work& w, cudaS
   g_launches = 0;
   LaunchCfg c{num_sms(), tm, &g_launches};
   switch (kt) {
+    case SS_U32: return run_u32(op, vt, P, w, st, c);
     case SS_U64: return run_u64(op, vt, P, w, st, c);
+    case SS_U128: return run_u128(op, vt, P, w, st, c);
     default: return cudaErrorNotSupported;
   }
 }

@@ -130,7 +130,7 @@ __device__ __forceinline__ uint32_t bucket_in(const K& k, const Seg& sg, const K
 // ----------------------------------------------------------------------------
 // init: reset the control block and seed level 0 (or a single base case).
 // ----------------------------------------------------------------------------
-__global__ void k_init(Work w) {
+static __global__ void k_init(Work w) {
   if (threadIdx.x != 0) return;
   Ctrl* c = w.ctrl;
   for (int l = 0; l < kMaxLevels; ++l) {
@@ -758,7 +758,7 @@ __global__ void __launch_bounds__(kDT, 2) k_distribute(Work w, LevelBufs lb) {
 // scan_items: one CTA.  Exclusive scans over the segments' item counts give
 // every segment its slice of the finish list and of the next level.
 // ----------------------------------------------------------------------------
-__global__ void __launch_bounds__(1024) k_scan_items(Work w, int level) {
+static __global__ void __launch_bounds__(1024) k_scan_items(Work w, int level) {
   __shared__ uint32_t tmp[33];
   __shared__ uint32_t carry[2];
   const uint32_t ns = w.ctrl->nsegs[level];
@@ -1305,7 +1305,7 @@ __global__ void __launch_bounds__(kRT, 2) k_finish_reduce(Work w) {
 // ----------------------------------------------------------------------------
 constexpr uint32_t kScanChunk = 4096;  // items per CTA (1024 threads x 4)
 
-__global__ void __launch_bounds__(1024) k_iscan_a(Work w) {
+static __global__ void __launch_bounds__(1024) k_iscan_a(Work w) {
   __shared__ uint64_t tmp[33];
   const uint32_t nfin = w.ctrl->nfin;
   const uint64_t c0 = (uint64_t)blockIdx.x * kScanChunk;
@@ -1321,7 +1321,7 @@ __global__ void __launch_bounds__(1024) k_iscan_a(Work w) {
   if (threadIdx.x == 0) w.block_sums[blockIdx.x] = tot;
 }
 
-__global__ void __launch_bounds__(1024) k_iscan_b(Work w) {
+static __global__ void __launch_bounds__(1024) k_iscan_b(Work w) {
   __shared__ uint64_t tmp[33];
   __shared__ uint64_t carry;
   const uint32_t nfin = w.ctrl->nfin;
@@ -1344,7 +1344,7 @@ __global__ void __launch_bounds__(1024) k_iscan_b(Work w) {
   }
 }
 
-__global__ void __launch_bounds__(1024) k_iscan_c(Work w) {
+static __global__ void __launch_bounds__(1024) k_iscan_c(Work w) {
   __shared__ uint64_t tmp[33];
   const uint32_t nfin = w.ctrl->nfin;
   const uint64_t c0 = (uint64_t)blockIdx.x * kScanChunk;
