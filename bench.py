@@ -174,6 +174,62 @@ def dram_traffic_per_launch(n):
         return None
 
 
+LESS_EXTRA = [("exponential", 1e-6), ("gaussian_mixture", 8)]
+
+
+def time_op(ss, sg, torch, name, keys, dists, vals, kout, vout, ws, n, stream):
+    """One warm-up call, then one timed call per input distribution (CUDA
+    events on the launching stream), for an operation other than the headline.
+    collect-reduce and histogram run on the ten headline distributions;
+    semisort_< on uniform-10^9, Zipf-1.2, floor(Exp(10^-6)) and an 8-component
+    Gaussian mixture."""
+    opt = ss.make_options(seed=1, flags=ss.FLAG_PHASE_TIMING)
+    nu = torch.zeros(1, dtype=torch.uint64, device="cuda")
+    names = [dist_name(d) for d in dists]
+    inputs = list(keys)
+    extra = []
+    if name == "semisort_less":
+        pick = [i for i, d in enumerate(dists) if d in (("uniform", 10**9), ("zipf", 1.2))]
+        inputs = [keys[i] for i in pick]
+        names = [names[i] for i in pick]
+        for kind, p in LESS_EXTRA:
+            t = sg.exponential(SEED, n, p) if kind == "exponential" else sg.gaussian_mixture(SEED, n, int(p))
+            extra.append(t)
+            inputs.append(t)
+            names.append(f"{kind}-{p:g}")
+
+    def call(k):
+        if name == "semisort_equal":
+            ss.semisort_equal(k, vals, keys_out=kout, vals_out=vout, workspace=ws, options=opt)
+        elif name == "semisort_less":
+            ss.semisort_less(k, vals, keys_out=kout, vals_out=vout, workspace=ws, options=opt)
+        elif name == "collect_reduce":
+            ss.collect_reduce(k, vals, capacity=n, ukeys_out=kout, sums_out=vout, num_unique=nu, workspace=ws,
+                              options=opt)
+        else:
+            ss.histogram(k, capacity=n, ukeys_out=kout, counts_out=vout.view(torch.uint32)[:n], num_unique=nu,
+                         workspace=ws, options=opt)
+
+    call(inputs[0])
+    torch.cuda.synchronize()
+    per, phases, total = {}, {}, 0.0
+    for k, nm in zip(inputs, names):
+        a = torch.cuda.Event(enable_timing=True)
+        b = torch.cuda.Event(enable_timing=True)
+        a.record(stream)
+        call(k)
+        b.record(stream)
+        b.synchronize()
+        per[nm] = a.elapsed_time(b)
+        total += per[nm]
+        for pn, pm in ss.phase_times():
+            phases[pn] = phases.get(pn, 0.0) + pm / len(inputs)
+    err = ss.last_device_error(ws)
+    del extra
+    return {"value": n * len(inputs) / (total / 1000.0) / 1e9, "unit": UNIT, "device_error": err,
+            "per_distribution_ms": per, "phase_ms": phases}
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -186,6 +242,8 @@ def main():
     ap.add_argument("--e2e-steps", type=int, default=3)
     ap.add_argument("--quick", action="store_true", help="small smoke configuration (not a bench number)")
     ap.add_argument("--dists", default="", help="comma-separated indices into the distribution list")
+    ap.add_argument("--ops", default="collect_reduce,histogram,semisort_less",
+                    help="further operations timed after the headline (empty: none)")
     args = ap.parse_args()
 
     rank = int(os.environ.get("RANK", "0"))
@@ -216,7 +274,11 @@ def main():
     kout = torch.empty(n, dtype=torch.uint64, device="cuda")
     vout = torch.empty(n, dtype=torch.uint64, device="cuda")
     opt = ss.make_options(seed=1, flags=ss.FLAG_PHASE_TIMING)
-    ws = ss.alloc_workspace(ss.OP_EQUAL, keys[0], vals, opt)
+    ops = [o for o in args.ops.split(",") if o]
+    op_codes = {"semisort_equal": ss.OP_EQUAL, "collect_reduce": ss.OP_REDUCE, "histogram": ss.OP_HIST,
+                "semisort_less": ss.OP_LESS}
+    ws_bytes = max(ss.workspace_size(op_codes[o], ss.SS_U64, ss.SS_U64, n, opt) for o in ["semisort_equal"] + ops)
+    ws = torch.empty(ws_bytes, dtype=torch.uint8, device="cuda")
     stream = torch.cuda.current_stream()
 
     def step(i):
@@ -305,6 +367,10 @@ def main():
                "d2h_bytes_per_step": 16 * n, "workload": f"semisort_equal n={n} {dist_name(d_e2e)}"}
         del hk, hv, hko, hvo
 
+    by_op = {}
+    for o in ops:
+        by_op[o] = time_op(ss, sg, torch, o, keys, dists, vals, kout, vout, ws, n, stream)
+
     if rank != 0:
         if world > 1:
             dist.destroy_process_group()
@@ -332,6 +398,7 @@ def main():
         "e2e": e2e,
         "gpu_launches": launches,
         "clocks": clk,
+        "other_ops": by_op,
     }
     print(json.dumps(line))
     if world > 1:

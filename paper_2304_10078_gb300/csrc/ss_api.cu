@@ -53,11 +53,17 @@ ss_status make_plan(int op, int kt, int vt, uint64_t n, const ss_options* opt, i
   uint32_t alpha = (opt && opt->alpha) ? opt->alpha : kAlphaMax;
   alpha = std::min(std::max(alpha, 64u), kAlphaMax);
   P->alpha = alpha;
+  // top-level light buckets: n_L ~ 2n / alpha, at most 2^9 hash buckets or 2^11
+  // semisort_< key ranges
+  // (semisort_< with 16-byte keys keeps the narrow top level: 2^8 ranges)
+  const bool wide = op == SS_OP_SEMISORT_LESS && P->kbytes < 16;
+  const uint32_t lb_max = wide ? (uint32_t)kLessTopLog2
+                               : op == SS_OP_SEMISORT_LESS ? (uint32_t)kMaxLightLog2 - 1 : (uint32_t)kMaxLightLog2;
   uint32_t lb1 = 0;
   if (opt && opt->n_light_log2)
-    lb1 = std::min<uint32_t>(std::max<uint32_t>(opt->n_light_log2, 1), kMaxLightLog2);
+    lb1 = std::min<uint32_t>(std::max<uint32_t>(opt->n_light_log2, 1), lb_max);
   else
-    lb1 = std::min<uint32_t>(std::max<uint32_t>(ceil_log2((2 * n + alpha - 1) / alpha), 1), kMaxLightLog2);
+    lb1 = std::min<uint32_t>(std::max<uint32_t>(ceil_log2((2 * n + alpha - 1) / alpha), 1), lb_max);
   P->lbits1 = lb1;
   uint64_t l1 = (n + 2 * (uint64_t)nsm - 1) / (2 * (uint64_t)nsm);
   l1 = ((l1 + 4095) / 4096) * 4096;
@@ -77,7 +83,7 @@ ss_status make_plan(int op, int kt, int vt, uint64_t n, const ss_options* opt, i
   const bool red = op == SS_OP_COLLECT_REDUCE || op == SS_OP_HISTOGRAM;
   // level 0: one segment; bucket rows per segment are n_L + n_H,cap (hash
   // buckets) or 4 n_L (semisort_<: 2q + 1 ids for q < 2 n_L boundaries)
-  const uint32_t nl0 = 1u << (less ? std::min<uint32_t>(lb1, kMaxLightLog2 - 1) : lb1);
+  const uint32_t nl0 = 1u << lb1;
   const uint32_t rows0 = less ? 4 * nl0 : nl0 + std::min<uint32_t>(nl0, kMaxHeavy);
   P->seg_cap[0] = 1;
   P->tile_cap[0] = (uint32_t)((n + P->l1 - 1) / P->l1);
@@ -148,6 +154,10 @@ ss_status make_plan(int op, int kt, int vt, uint64_t n, const ss_options* opt, i
   o = al(o + (op == SS_OP_COLLECT_REDUCE ? (size_t)P->item_cap * 8 : 0));
   P->off_scratch32 = o;
   o = al(o + (op == SS_OP_HISTOGRAM ? (size_t)n * 4 : 0));
+  P->off_bigs = o;
+  o = al(o + (wide && multi ? (size_t)kBigSample * P->kbytes : 0));
+  P->off_bigs_tmp = o;
+  o = al(o + (wide && multi ? (size_t)kBigSample * P->kbytes : 0));
   P->off_ctrl = 0;
   P->total = o;
   return SS_OK;
@@ -189,6 +199,8 @@ void fill_work(const Plan& P, void* ws, Work* w) {
   w->block_sums = reinterpret_cast<uint64_t*>(b + P.off_block_sums);
   w->item_aux = reinterpret_cast<uint64_t*>(b + P.off_item_aux);
   w->scratch32 = reinterpret_cast<uint32_t*>(b + P.off_scratch32);
+  w->bigs = b + P.off_bigs;
+  w->bigs_tmp = b + P.off_bigs_tmp;
   w->ctrl = reinterpret_cast<Ctrl*>(b + P.off_ctrl);
 }
 

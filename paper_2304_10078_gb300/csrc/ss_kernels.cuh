@@ -111,6 +111,14 @@ __device__ __forceinline__ uint32_t bucket_less(const K& k, const K* bnd, const 
   return 2 * lo;
 }
 
+// Whether the semisort_< top level uses the wide bucket space (2^16-key
+// sample, up to 2^11 ranges): for keys up to 8 bytes, whose wide distribute
+// buffers fit in shared memory.
+template <class K, int OP>
+struct TopWide {
+  static constexpr bool value = OP == kOpLess && sizeof(K) < 16;
+};
+
 // Whether bucket b holds a single heavy key (final after distribution).
 template <int OP>
 __device__ __forceinline__ bool is_heavy(uint32_t b, uint32_t nl) {
@@ -189,7 +197,7 @@ __global__ void __launch_bounds__(1024) k_plan(Work w, int level) {
         lb = want <= 2 ? 1u : (uint32_t)(64 - __clzll(want - 1));
         lb = lb > (uint32_t)kMaxLightLog2 ? (uint32_t)kMaxLightLog2 : lb;
       }
-      if (OP == kOpLess && lb > kMaxLightLog2 - 1) lb = kMaxLightLog2 - 1;
+      if (OP == kOpLess && level > 0 && lb > kMaxLightLog2 - 1) lb = kMaxLightLog2 - 1;
       const uint32_t nl = 1u << lb;
       sg.lbits = lb;
       // semisort_<: q <= (n_L - 1) + n_L boundaries give 2q + 1 < 4 n_L bucket ids
@@ -261,6 +269,7 @@ __global__ void __launch_bounds__(1024) k_sample(Work w, LevelBufs lb, uint32_t 
   __shared__ uint32_t tab[4 * kMaxHeavy];
   __shared__ uint32_t tmp[33];
   __shared__ uint32_t nh_sh;
+  if (TopWide<K, OP>::value && lb.level == 0) return;  // the wide top level uses k_less_split
   const uint32_t ns = w.ctrl->nsegs[lb.level];
   for (uint32_t s = blockIdx.x; s < ns; s += gridDim.x) {
     const Seg sg = w.segs[lb.level][s];
@@ -372,6 +381,150 @@ __global__ void __launch_bounds__(1024) k_sample(Work w, LevelBufs lb, uint32_t 
   }
 }
 
+// ----------------------------------------------------------------------------
+// semisort_< top level: a sample of kBigSample keys, sorted on the device.
+// Each CTA gathers one run of the sample at seeded positions and sorts it in
+// shared memory (bitonic); a merge kernel then places every key at its rank
+// in the whole sample (positions inside its run plus, in every other run, the
+// keys that order before it -- ties go to the earlier run), a stable merge.
+// ----------------------------------------------------------------------------
+template <class K>
+struct BigRun {
+  static constexpr uint32_t len = sizeof(K) >= 16 ? 8192u : 16384u;  // keys per sorted run
+  static constexpr uint32_t runs = kBigSample / len;
+};
+
+template <class K>
+__global__ void __launch_bounds__(1024) k_bigsample_sort(Work w) {
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  K* S = reinterpret_cast<K*>(smem_raw);
+  constexpr uint32_t L = BigRun<K>::len;
+  const K* in = reinterpret_cast<const K*>(w.in_k);
+  const uint64_t base = mix64(level_salt(w.seed, 0) ^ 0xB165A3F1E5EEDull);
+  for (uint32_t t = threadIdx.x; t < L; t += blockDim.x) {
+    const uint64_t gi = (uint64_t)blockIdx.x * L + t;
+    const uint64_t r = mix64(base + (gi + 1) * 0x9E3779B97F4A7C15ull);
+    S[t] = in[__umul64hi(r, w.n)];
+  }
+  __syncthreads();
+  for (uint32_t k = 2; k <= L; k <<= 1) {
+    for (uint32_t j = k >> 1; j > 0; j >>= 1) {
+      for (uint32_t p = threadIdx.x; p < L / 2; p += blockDim.x) {
+        const uint32_t i = ((p & ~(j - 1)) << 1) | (p & (j - 1));
+        const K a = S[i], b = S[i + j];
+        if ((i & k) == 0 ? KeyT<K>::lt(b, a) : KeyT<K>::lt(a, b)) {
+          S[i] = b;
+          S[i + j] = a;
+        }
+      }
+      __syncthreads();
+    }
+  }
+  K* out = reinterpret_cast<K*>(w.bigs_tmp) + (uint64_t)blockIdx.x * L;
+  for (uint32_t t = threadIdx.x; t < L; t += blockDim.x) out[t] = S[t];
+}
+
+template <class K>
+__global__ void __launch_bounds__(256) k_bigsample_merge(Work w) {
+  constexpr uint32_t L = BigRun<K>::len;
+  const uint32_t e = blockIdx.x * blockDim.x + threadIdx.x;
+  if (e >= kBigSample) return;
+  const K* runs = reinterpret_cast<const K*>(w.bigs_tmp);
+  const uint32_t r = e / L;
+  const K key = runs[e];
+  uint32_t rank = e % L;
+  for (uint32_t q = 0; q < BigRun<K>::runs; ++q) {
+    if (q == r) continue;
+    const K* R = runs + (uint64_t)q * L;
+    uint32_t lo = 0, hi = L;  // earlier runs: keys <= key; later runs: keys < key
+    while (lo < hi) {
+      const uint32_t mid = (lo + hi) >> 1;
+      const bool before = q < r ? !KeyT<K>::lt(key, R[mid]) : KeyT<K>::lt(R[mid], key);
+      if (before)
+        lo = mid + 1;
+      else
+        hi = mid;
+    }
+    rank += lo;
+  }
+  reinterpret_cast<K*>(w.bigs)[rank] = key;
+}
+
+// Boundaries of the semisort_< top level from the sorted sample: n_L - 1
+// splitters at evenly spaced sample ranks (or, in learned mode, the integer
+// splitters the CDF model produced, see k_learn_*) merged with the heavy keys
+// -- keys whose sample run reaches the expected size of one range bucket,
+// at most kMaxHeavy of them in key order -- into one sorted list with a flag
+// per heavy key (equality buckets, as in k_sample).  One CTA.
+template <class K>
+__global__ void __launch_bounds__(1024) k_less_split(Work w, const K* learned) {
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  __shared__ uint32_t tmp[33];
+  __shared__ uint32_t nh_sh;
+  Seg* sgp = w.segs[0];
+  if (w.ctrl->nsegs[0] == 0 || sgp[0].lbits == 0) return;
+  const uint32_t nl = 1u << sgp[0].lbits;
+  const uint32_t hcap = hcap_of(sgp[0].lbits);
+  const K* S = reinterpret_cast<const K*>(w.bigs);
+  uint32_t tau = kBigSample / nl;
+  if (tau < 2) tau = 2;
+  K* cs = reinterpret_cast<K*>(smem_raw);  // n_L - 1 candidate splitters
+  K* hs = cs + nl;                         // heavy keys (at most hcap)
+  for (uint32_t j = 1 + threadIdx.x; j < nl; j += blockDim.x)
+    cs[j - 1] = learned ? learned[j - 1] : S[(uint64_t)j * kBigSample / nl];
+  if (threadIdx.x == 0) nh_sh = 0;
+  __syncthreads();
+  for (uint32_t t0 = 0; t0 < kBigSample; t0 += blockDim.x) {
+    const uint32_t t = t0 + threadIdx.x;
+    const uint32_t f = (t < kBigSample && (t == 0 || !KeyT<K>::eq(S[t], S[t - 1])) && t + tau - 1 < kBigSample &&
+                        KeyT<K>::eq(S[t + tau - 1], S[t]))
+                           ? 1u
+                           : 0u;
+    uint32_t tot;
+    const uint32_t ex = block_exclusive_scan(f, tmp, &tot);
+    if (f && nh_sh + ex < hcap) hs[nh_sh + ex] = S[t];
+    __syncthreads();
+    if (threadIdx.x == 0) nh_sh += tot;
+    __syncthreads();
+  }
+  const uint32_t nh = nh_sh < hcap ? nh_sh : hcap;
+  if (threadIdx.x == 0) {
+    // q <= (n_L - 1) + hcap < 2 n_L boundaries: within the segment's 4 n_L rows
+    K* bnd = reinterpret_cast<K*>(w.splitters[0]) + sgp[0].bbase;
+    uint16_t* fl = w.htab[0] + 2ull * sgp[0].bbase;
+    uint32_t q = 0, j = 0, hi = 0;
+    bool have_last = false;
+    K last = cs[0];
+    while (j + 1 < nl || hi < nh) {
+      K c;
+      bool heavy;
+      if (j + 1 < nl && (hi >= nh || KeyT<K>::lt(cs[j], hs[hi]))) {
+        c = cs[j++];
+        heavy = false;
+      } else if (j + 1 < nl && KeyT<K>::eq(cs[j], hs[hi])) {
+        c = hs[hi++];
+        ++j;
+        heavy = true;
+      } else {
+        c = hs[hi++];
+        heavy = true;
+      }
+      if (have_last && KeyT<K>::eq(c, last)) {
+        if (heavy) fl[q - 1] = 1;
+        continue;
+      }
+      bnd[q] = c;
+      fl[q] = heavy ? 1 : 0;
+      ++q;
+      last = c;
+      have_last = true;
+    }
+    sgp[0].nh = q;
+    sgp[0].nb = 2 * q + 1;
+    w.ctrl->stats[7] = nh;
+  }
+}
+
 // Load a segment's heavy keys and table (semisort_<: boundaries and flags)
 // into shared memory.
 template <class K, int OP>
@@ -400,12 +553,30 @@ __device__ __forceinline__ void load_heavy(const Work& w, int level, const Seg& 
 // ----------------------------------------------------------------------------
 constexpr int kCountThreads = 512;
 
-template <class K, class V, int OP>
+// Bucket-id space of a level: the wide semisort_< top level (BIG) or the rest.
+template <bool BIG>
+struct Space {
+  static constexpr uint32_t kIds = BIG ? kBigBuckets : kMaxBuckets;   // bucket ids
+  static constexpr uint32_t kBnd = BIG ? kBigBounds : kMaxHeavy;      // heavy keys / boundaries
+  static constexpr uint32_t kTab = kBnd > 4 * kMaxHeavy ? kBnd : 4 * kMaxHeavy;  // table / flags
+};
+
+template <class K, int OP, bool BIG>
+struct CountSmem {
+  uint32_t hist[Space<BIG>::kIds];
+  K hk[Space<BIG>::kBnd];
+  uint16_t ht[Space<BIG>::kTab];
+  unsigned long long hsum[OP == kOpReduce ? kMaxHeavy : 1];
+};
+
+template <class K, class V, int OP, bool BIG>
 __global__ void __launch_bounds__(kCountThreads) k_count(Work w, LevelBufs lb) {
-  __shared__ uint32_t hist[kMaxBuckets];
-  __shared__ K hk[kMaxHeavy];
-  __shared__ uint16_t ht[4 * kMaxHeavy];
-  __shared__ unsigned long long hsum[OP == kOpReduce ? kMaxHeavy : 1];
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  CountSmem<K, OP, BIG>& cs = *reinterpret_cast<CountSmem<K, OP, BIG>*>(smem_raw);
+  uint32_t* hist = cs.hist;
+  K* hk = cs.hk;
+  uint16_t* ht = cs.ht;
+  unsigned long long* hsum = cs.hsum;
   const uint32_t nt = w.ctrl->ntiles[lb.level];
   for (uint32_t t = blockIdx.x; t < nt; t += gridDim.x) {
     const Tile tl = w.tiles[lb.level][t];
@@ -545,6 +716,7 @@ template <int OP>
 __global__ void __launch_bounds__(1024) k_scan(Work w, LevelBufs lb) {
   __shared__ uint32_t tmp[33];
   __shared__ uint32_t carry;
+  __shared__ uint32_t szs[OP == kOpLess ? kBigBuckets : kMaxBuckets];  // bucket sizes
   const uint32_t ns = w.ctrl->nsegs[lb.level];
   const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5, nw = blockDim.x >> 5;
   const bool last_level = lb.level == kMaxLevels - 1;
@@ -572,7 +744,10 @@ __global__ void __launch_bounds__(1024) k_scan(Work w, LevelBufs lb) {
         if (i < sg.ntiles) row[i] = run + inc - v;
         run += __shfl_sync(kFull, inc, 31);
       }
-      if (lane == 0) bsize[b] = run;
+      if (lane == 0) {
+        bsize[b] = run;
+        szs[b] = run;
+      }
     }
     __syncthreads();
     if (threadIdx.x == 0) carry = 0;
@@ -600,7 +775,7 @@ __global__ void __launch_bounds__(1024) k_scan(Work w, LevelBufs lb) {
     const uint32_t tf = block_reduce_sum(nfin, tmp);
     const uint32_t tn = block_reduce_sum(nnext, tmp);
     if (threadIdx.x == 0) {
-      const uint32_t nw = refine_windows<OP>(bsize, boff, nl, nb, w.alpha, last_level, sg.start, lb.dst_id,
+      const uint32_t nw = refine_windows<OP>(szs, boff, nl, nb, w.alpha, last_level, sg.start, lb.dst_id,
                                              lb.level, nullptr, 0, 0);
       w.segs[lb.level][s].cnt_fin = tf + nw;
       w.segs[lb.level][s].cnt_next = tn;
@@ -626,14 +801,14 @@ constexpr int kDR = 16;
 constexpr int kDCH = kDT * kDR;  // 4096 records per chunk
 using DRank = BlockRank<kDT, kDR, 5>;
 
-template <class K, class V>
+template <class K, class V, bool BIG>
 struct DistSmem {
   RecT<K, V> S[kDCH];                // the chunk, swizzled (sw)
   typename DRank::Smem rk;
   uint32_t px[kDCH + kDCH / 32];     // (bucket << 16 | chunk index) at rank, padded (bpad)
-  uint32_t cur[kMaxBuckets];         // next write offset per bucket within the segment
-  K hk[kMaxHeavy];
-  uint16_t ht[4 * kMaxHeavy];
+  uint32_t cur[Space<BIG>::kIds];    // next write offset per bucket within the segment
+  K hk[Space<BIG>::kBnd];
+  uint16_t ht[Space<BIG>::kTab];
 };
 
 // Record i of a level's source (caller SoA at level 0, AoS records after).
@@ -670,10 +845,10 @@ __device__ __forceinline__ void load_chunk(RecT<K, V>* S, uint32_t len, Src src)
   }
 }
 
-template <class K, class V, int OP>
+template <class K, class V, int OP, bool BIG>
 __global__ void __launch_bounds__(kDT, 2) k_distribute(Work w, LevelBufs lb) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
-  DistSmem<K, V>& sm = *reinterpret_cast<DistSmem<K, V>*>(smem_raw);
+  DistSmem<K, V, BIG>& sm = *reinterpret_cast<DistSmem<K, V, BIG>*>(smem_raw);
   using Rec = RecT<K, V>;
   constexpr int RB = sizeof(Rec);
   constexpr bool kVals = !std::is_same<V, void>::value;
@@ -695,28 +870,27 @@ __global__ void __launch_bounds__(kDT, 2) k_distribute(Work w, LevelBufs lb) {
       const uint32_t* boff = w.boff[lb.level] + sg.bbase;
       for (uint32_t b = tid; b < nb; b += kDT) sm.cur[b] = boff[b] + X[(uint64_t)b * sg.ntiles + tl.idx];
     }
-    const bool two_pass = nb > 32;
+    const int passes = nb > 1024 ? 3 : nb > 32 ? 2 : 1;
     for (uint32_t c0 = 0; c0 < tl.len; c0 += kDCH) {
       const uint32_t clen = tl.len - c0 < (uint32_t)kDCH ? tl.len - c0 : (uint32_t)kDCH;
       const uint64_t gbase = tl.start + c0;
       load_chunk<kDT, K, V>(sm.S, clen, [&](uint32_t i) { return read_src<K, V>(lb, gbase + i); });
       __syncthreads();
       uint32_t bid[kDR], rk[kDR];
-      // invalid slots get the largest bucket id: both 5-bit digits are 31, and
-      // as the last items in blocked order they rank after every valid record
+      // invalid slots get id 2^15 - 1: every 5-bit digit is 31, and as the last
+      // items in blocked order they rank after every valid record
 #pragma unroll
       for (int r = 0; r < kDR; ++r)
-        bid[r] = c0t + r < clen ? bucket_in<K, OP>(sm.S[sw<RB>(c0t + r)].k, sg, sm.hk, sm.ht, tmask)
-                                : (kMaxBuckets - 1);
+        bid[r] = c0t + r < clen ? bucket_in<K, OP>(sm.S[sw<RB>(c0t + r)].k, sg, sm.hk, sm.ht, tmask) : 0x7FFFu;
       DRank::rank(sm.rk, bid, 0, rk);
 #pragma unroll
       for (int r = 0; r < kDR; ++r) sm.px[bpad(rk[r])] = (bid[r] << 16) | (c0t + r);
-      if (two_pass) {
+      for (int pz = 1; pz < passes; ++pz) {
         __syncthreads();
         uint32_t x[kDR];
 #pragma unroll
         for (int r = 0; r < kDR; ++r) x[r] = sm.px[bpad(c0t + r)];
-        DRank::rank(sm.rk, x, 21, rk);
+        DRank::rank(sm.rk, x, 16 + 5 * pz, rk);
 #pragma unroll
         for (int r = 0; r < kDR; ++r) sm.px[bpad(rk[r])] = x[r];
       }
@@ -806,6 +980,7 @@ template <int OP>
 __global__ void __launch_bounds__(1024) k_emit(Work w, LevelBufs lb) {
   __shared__ uint32_t tmp[33];
   __shared__ uint32_t carry[2];
+  __shared__ uint32_t szs[OP == kOpLess ? kBigBuckets : kMaxBuckets];  // bucket sizes
   const uint32_t ns = w.ctrl->nsegs[lb.level];
   const bool last_level = lb.level == kMaxLevels - 1;
   for (uint32_t s = blockIdx.x; s < ns; s += gridDim.x) {
@@ -815,11 +990,13 @@ __global__ void __launch_bounds__(1024) k_emit(Work w, LevelBufs lb) {
     const uint32_t nb = sg.nb;
     const uint32_t* bsize = w.bsize[lb.level] + sg.bbase;
     const uint32_t* boff = w.boff[lb.level] + sg.bbase;
+    for (uint32_t b = threadIdx.x; b < nb; b += blockDim.x) szs[b] = bsize[b];
+    __syncthreads();
     if (threadIdx.x == 0) {
-      const uint32_t nw = refine_windows<OP>(bsize, boff, nl, nb, w.alpha, last_level, sg.start, lb.dst_id,
+      const uint32_t nw = refine_windows<OP>(szs, boff, nl, nb, w.alpha, last_level, sg.start, lb.dst_id,
                                              lb.level, w.items, sg.fin_off, w.item_cap);
       for (uint32_t b = 0; b < nb; ++b)
-        if (!is_heavy<OP>(b, nl) && bsize[b] > w.alpha && last_level) set_error(w.ctrl, 8 /*SS_ERR_DEPTH*/);
+        if (!is_heavy<OP>(b, nl) && szs[b] > w.alpha && last_level) set_error(w.ctrl, 8 /*SS_ERR_DEPTH*/);
       carry[0] = sg.fin_off + nw;
       carry[1] = sg.next_off;
     }

@@ -49,10 +49,27 @@ template <class K, class V, int OP>
 cudaError_t launch_pipeline(const Plan& P, const Work& w, cudaStream_t st, const LaunchCfg& cfg) {
   PhaseTimer* tm = cfg.timer;
   const int nsm = cfg.num_sms;
-  const size_t dist_smem = sizeof(DistSmem<K, V>);
+  constexpr bool kWide = TopWide<K, OP>::value;  // semisort_< top level in the wide bucket space
+  constexpr size_t kSmemMax = 232448;              // opt-in shared memory per block (sm_103a)
+  static_assert(sizeof(DistSmem<K, V, false>) <= kSmemMax && sizeof(DistSmem<K, V, kWide>) <= kSmemMax, "smem");
+  static_assert(sizeof(CountSmem<K, OP, kWide>) <= kSmemMax && sizeof(RefSmem<K, V>) <= kSmemMax, "smem");
+  static_assert(sizeof(LessSmem<K, V>) <= kSmemMax && sizeof(RedSmem<K>) <= kSmemMax, "smem");
+  const size_t dist_smem = sizeof(DistSmem<K, V, false>);
+  const size_t dist_smem_top = sizeof(DistSmem<K, V, kWide>);
+  const size_t count_smem = sizeof(CountSmem<K, OP, false>);
+  const size_t count_smem_top = sizeof(CountSmem<K, OP, kWide>);
   size_t ref_smem = 0;
   cudaError_t e;
-  if ((e = set_smem(k_distribute<K, V, OP>, dist_smem)) != cudaSuccess) return e;
+  if ((e = set_smem(k_distribute<K, V, OP, false>, dist_smem)) != cudaSuccess) return e;
+  if ((e = set_smem(k_distribute<K, V, OP, kWide>, dist_smem_top)) != cudaSuccess) return e;
+  if ((e = set_smem(k_count<K, V, OP, false>, count_smem)) != cudaSuccess) return e;
+  if ((e = set_smem(k_count<K, V, OP, kWide>, count_smem_top)) != cudaSuccess) return e;
+  const size_t bigs_smem = (size_t)BigRun<K>::len * sizeof(K);
+  const size_t split_smem = ((size_t)(1u << kLessTopLog2) + kMaxHeavy) * sizeof(K);
+  if constexpr (kWide) {
+    if ((e = set_smem(k_bigsample_sort<K>, bigs_smem)) != cudaSuccess) return e;
+    if ((e = set_smem(k_less_split<K>, split_smem)) != cudaSuccess) return e;
+  }
   if constexpr (OP == kOpEqual) {
     ref_smem = sizeof(RefSmem<K, V>);
     if ((e = set_smem(k_finish_equal<K, V>, ref_smem)) != cudaSuccess) return e;
@@ -76,20 +93,35 @@ cudaError_t launch_pipeline(const Plan& P, const Work& w, cudaStream_t st, const
       const uint32_t segs = P.seg_cap[level];
       const uint32_t tiles = P.tile_cap[level];
       auto cap = [](uint32_t want, uint32_t lim) { return want < lim ? (want ? want : 1) : lim; };
+      const bool top_wide = kWide && level == 0;
       k_plan<OP><<<1, 1024, 0, st>>>(w, level);
       if (tm) tm->mark(level == 0 ? "plan.L0" : "plan.L1+");
-      const uint32_t s_cap = level == 0 ? P.s1 : P.s2;
-      k_sample<K, V, OP><<<cap(segs, nsm * 2), 1024, (size_t)s_cap * sizeof(K), st>>>(w, lb, s_cap);
+      if (top_wide) {
+        k_bigsample_sort<K><<<BigRun<K>::runs, 1024, bigs_smem, st>>>(w);
+        k_bigsample_merge<K><<<kBigSample / 256, 256, 0, st>>>(w);
+        k_less_split<K><<<1, 1024, split_smem, st>>>(w, nullptr);
+        nl += 3;
+      } else {
+        const uint32_t s_cap = level == 0 ? P.s1 : P.s2;
+        k_sample<K, V, OP><<<cap(segs, nsm * 2), 1024, (size_t)s_cap * sizeof(K), st>>>(w, lb, s_cap);
+        ++nl;
+      }
       if (tm) tm->mark(level == 0 ? "sample.L0" : "sample.L1+");
-      k_count<K, V, OP><<<cap(tiles, nsm * 4), kCountThreads, 0, st>>>(w, lb);
+      if (top_wide)
+        k_count<K, V, OP, kWide><<<cap(tiles, nsm * 4), kCountThreads, count_smem_top, st>>>(w, lb);
+      else
+        k_count<K, V, OP, false><<<cap(tiles, nsm * 4), kCountThreads, count_smem, st>>>(w, lb);
       if (tm) tm->mark(level == 0 ? "count.L0" : "count.L1+");
       k_scan<OP><<<cap(segs, nsm * 2), 1024, 0, st>>>(w, lb);
       if (tm) tm->mark(level == 0 ? "scan.L0" : "scan.L1+");
-      k_distribute<K, V, OP><<<cap(tiles, nsm * 2), kDT, dist_smem, st>>>(w, lb);
+      if (top_wide)
+        k_distribute<K, V, OP, kWide><<<cap(tiles, nsm * 2), kDT, dist_smem_top, st>>>(w, lb);
+      else
+        k_distribute<K, V, OP, false><<<cap(tiles, nsm * 2), kDT, dist_smem, st>>>(w, lb);
       if (tm) tm->mark(level == 0 ? "distribute.L0" : "distribute.L1+");
       k_scan_items<<<1, 1024, 0, st>>>(w, level);
       k_emit<OP><<<cap(segs, nsm * 2), 1024, 0, st>>>(w, lb);
-      nl += 7;
+      nl += 6;
       if (tm) tm->mark(level == 0 ? "emit.L0" : "emit.L1+");
     }
   }

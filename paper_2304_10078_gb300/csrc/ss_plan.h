@@ -16,6 +16,13 @@ constexpr int kMaxLightLog2 = 9;       // n_L <= 512 per segment
 constexpr uint32_t kMaxHeavy = 512;    // heavy keys per segment
 constexpr uint32_t kMaxBuckets = 1024; // n_L + heavy: bucket ids fit two 5-bit rank passes
 constexpr uint32_t kCopyChunk = 1u << 16;  // records per copy item
+// semisort_< top level: up to 2^11 key ranges cut from a 2^16-key sample; with
+// up to 512 heavy equality buckets the 2q + 1 bucket ids stay below 2^13 and
+// are ranked in three 5-bit passes.
+constexpr int kLessTopLog2 = 11;
+constexpr uint32_t kBigBuckets = 8192;
+constexpr uint32_t kBigBounds = (1u << kLessTopLog2) + kMaxHeavy;
+constexpr uint32_t kBigSample = 1u << 16;
 
 // Operations.
 enum Op : int { kOpEqual = 0, kOpLess = 1, kOpReduce = 2, kOpHist = 3 };
@@ -114,6 +121,8 @@ struct Work {
   uint64_t* num_unique; // user pointer (collect-reduce / histogram)
   void* sums_out;       // user pointer: u64 sums or u32 counts
   void* splitters[kMaxLevels];  // semisort_<: per-segment sorted boundaries at bbase
+  void* bigs;           // semisort_<: the sorted top-level sample (kBigSample keys)
+  void* bigs_tmp;       // its sorted runs before the merge
   uint32_t* scratch32;  // histogram: per-position counts of compacted base cases
   uint64_t* item_aux;   // collect-reduce: heavy totals per item
   uint64_t out_capacity;
@@ -133,6 +142,7 @@ struct Plan {
       off_htab[kMaxLevels], off_bsize[kMaxLevels], off_boff[kMaxLevels], off_hpart[kMaxLevels],
       off_split[kMaxLevels];
   size_t off_items, off_item_out, off_item_pos, off_block_sums, off_ctrl, off_scratch32, off_item_aux;
+  size_t off_bigs, off_bigs_tmp;
   size_t total;
 };
 
