@@ -183,12 +183,13 @@ def time_op(ss, sg, torch, name, keys, dists, vals, kout, vout, ws, n, stream):
     collect-reduce and histogram run on the ten headline distributions;
     semisort_< on uniform-10^9, Zipf-1.2, floor(Exp(10^-6)) and an 8-component
     Gaussian mixture."""
-    opt = ss.make_options(seed=1, flags=ss.FLAG_PHASE_TIMING)
+    learned = name == "semisort_less_learned"
+    opt = ss.make_options(seed=1, flags=ss.FLAG_PHASE_TIMING, splitter_mode=1 if learned else 0)
     nu = torch.zeros(1, dtype=torch.uint64, device="cuda")
     names = [dist_name(d) for d in dists]
     inputs = list(keys)
     extra = []
-    if name == "semisort_less":
+    if name.startswith("semisort_less"):
         pick = [i for i, d in enumerate(dists) if d in (("uniform", 10**9), ("zipf", 1.2))]
         inputs = [keys[i] for i in pick]
         names = [names[i] for i in pick]
@@ -201,7 +202,7 @@ def time_op(ss, sg, torch, name, keys, dists, vals, kout, vout, ws, n, stream):
     def call(k):
         if name == "semisort_equal":
             ss.semisort_equal(k, vals, keys_out=kout, vals_out=vout, workspace=ws, options=opt)
-        elif name == "semisort_less":
+        elif name.startswith("semisort_less"):
             ss.semisort_less(k, vals, keys_out=kout, vals_out=vout, workspace=ws, options=opt)
         elif name == "collect_reduce":
             ss.collect_reduce(k, vals, capacity=n, ukeys_out=kout, sums_out=vout, num_unique=nu, workspace=ws,
@@ -212,7 +213,7 @@ def time_op(ss, sg, torch, name, keys, dists, vals, kout, vout, ws, n, stream):
 
     call(inputs[0])
     torch.cuda.synchronize()
-    per, phases, total = {}, {}, 0.0
+    per, phases, total, balance = {}, {}, 0.0, {}
     for k, nm in zip(inputs, names):
         a = torch.cuda.Event(enable_timing=True)
         b = torch.cuda.Event(enable_timing=True)
@@ -224,10 +225,18 @@ def time_op(ss, sg, torch, name, keys, dists, vals, kout, vout, ws, n, stream):
         total += per[nm]
         for pn, pm in ss.phase_times():
             phases[pn] = phases.get(pn, 0.0) + pm / len(inputs)
+        if name.startswith("semisort_less"):
+            st = ss.stats(ws)
+            balance[nm] = {"splitters": ["sampled", "learned", "learned rejected"][st["l0_splitters"]],
+                           "max_light_bucket_over_mean": st["l0_max_light_bucket"] / (n / 2048.0),
+                           "records_at_level3": st["dist_l2"]}
     err = ss.last_device_error(ws)
     del extra
-    return {"value": n * len(inputs) / (total / 1000.0) / 1e9, "unit": UNIT, "device_error": err,
-            "per_distribution_ms": per, "phase_ms": phases}
+    out = {"value": n * len(inputs) / (total / 1000.0) / 1e9, "unit": UNIT, "device_error": err,
+           "per_distribution_ms": per, "phase_ms": phases}
+    if balance:
+        out["top_level_balance"] = balance
+    return out
 
 
 def main():
@@ -242,7 +251,7 @@ def main():
     ap.add_argument("--e2e-steps", type=int, default=3)
     ap.add_argument("--quick", action="store_true", help="small smoke configuration (not a bench number)")
     ap.add_argument("--dists", default="", help="comma-separated indices into the distribution list")
-    ap.add_argument("--ops", default="collect_reduce,histogram,semisort_less",
+    ap.add_argument("--ops", default="collect_reduce,histogram,semisort_less,semisort_less_learned",
                     help="further operations timed after the headline (empty: none)")
     args = ap.parse_args()
 
@@ -276,7 +285,7 @@ def main():
     opt = ss.make_options(seed=1, flags=ss.FLAG_PHASE_TIMING)
     ops = [o for o in args.ops.split(",") if o]
     op_codes = {"semisort_equal": ss.OP_EQUAL, "collect_reduce": ss.OP_REDUCE, "histogram": ss.OP_HIST,
-                "semisort_less": ss.OP_LESS}
+                "semisort_less": ss.OP_LESS, "semisort_less_learned": ss.OP_LESS}
     ws_bytes = max(ss.workspace_size(op_codes[o], ss.SS_U64, ss.SS_U64, n, opt) for o in ["semisort_equal"] + ops)
     ws = torch.empty(ws_bytes, dtype=torch.uint8, device="cuda")
     stream = torch.cuda.current_stream()

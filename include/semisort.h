@@ -151,6 +151,39 @@ ss_status semisort_equal_noalloc(ss_type key_type, ss_type val_type, const void*
                                  const void* vals, void* keys_out, void* vals_out, uint64_t n,
                                  const ss_options* opt, ss_stream_t stream);
 
+/* The learned-splitter model on its own.  semisort_less with
+ * options.splitter_mode = 1 fits a monotone CDF model to its 2^16-key top-level
+ * sample and inverts it into the top level's splitters (a gain in load
+ * balance only: bucketing stays exact key comparison).  The model is a 1-32-32-1
+ * perceptron in FP32 with softplus-positive weights and logistic hidden units;
+ * SS_MLP_PARAMS parameters laid out v1[32] | c1[32] | v2[32*32] (row j: the
+ * weights into hidden unit j of layer 2) | c2[32] | v3[32] | c3, with weights
+ * w = softplus(v).  Inputs are keys normalized to [0, 1]; targets are ranks
+ * divided by the sample size.  Each entry point needs a device workspace of
+ * ss_mlp_workspace_size() bytes (16-byte aligned) and is stream-ordered. */
+#define SS_MLP_PARAMS 1153
+size_t ss_mlp_workspace_size(void);
+
+/* Mean squared error over m <= 4096 points (x[m], t[m], device floats) and its
+ * gradient with respect to the parameters: d_out[0..1153) = gradient,
+ * d_out[1153] = loss.  Sums run in a fixed order (deterministic). */
+ss_status ss_mlp_loss_grad(const float* d_params, const float* d_x, const float* d_t, uint32_t m,
+                           float* d_out, void* ws, size_t ws_bytes, ss_stream_t stream);
+
+/* `steps` full-batch Adam steps (beta1 0.9, beta2 0.999, eps 1e-8, learning
+ * rate lr) from d_params0; writes the trained parameters and the loss at them. */
+ss_status ss_mlp_train(const float* d_x, const float* d_t, uint32_t m, const float* d_params0,
+                       uint32_t steps, float lr, float* d_params_out, float* d_loss_out, void* ws,
+                       size_t ws_bytes, ss_stream_t stream);
+
+/* Splitter j (1 <= j < 2^n_light_log2, n_light_log2 <= 11): the smallest key k
+ * in [kmin, kmax] with f((k - kmin) / (kmax - kmin)) >= j / 2^n_light_log2 (kmax if
+ * none), by bisection over the integer keys, f evaluated in FP32.  Keys SS_U32
+ * or SS_U64; d_splitters receives 2^n_light_log2 - 1 keys. */
+ss_status ss_mlp_invert(const float* d_params, ss_type key_type, uint64_t kmin, uint64_t kmax,
+                        uint32_t n_light_log2, void* d_splitters, void* ws, size_t ws_bytes,
+                        ss_stream_t stream);
+
 /* Reads (and clears) the device error flag left in `ws` by earlier calls on
  * `stream`; synchronizes the stream.  *code receives the ss_status of the
  * first device-side failure (SS_OK if none). */
@@ -160,7 +193,10 @@ ss_status ss_last_device_error(void* ws, ss_stream_t stream, int* code);
  * stream).  out[0..count) receives, in order: levels used, records distributed
  * at levels 1..4 (4 entries), records refined, records copied, heavy keys at
  * level 1, largest refined bucket, refine items, records whose bucket was all
- * distinct keys.  Returns the number of entries written. */
+ * distinct keys, splitters of the semisort_< top level (0 sampled, 1 learned,
+ * 2 learned but rejected on the sample), the largest top-level range bucket's
+ * count in the 2^16-key sample, the largest top-level light bucket in records.
+ * Returns the number of entries written. */
 int ss_get_stats(void* ws, ss_stream_t stream, uint64_t* out, int count);
 
 /* Per-kernel timings (milliseconds) of the last call made with

@@ -29,7 +29,8 @@ STATUS = {
 }
 
 STAT_NAMES = ["levels", "dist_l0", "dist_l1", "dist_l2", "dist_l3", "refined", "copied",
-              "heavy_l0", "max_refine", "refine_items", "all_distinct", "left_in_place"]
+              "heavy_l0", "max_refine", "refine_items", "all_distinct", "l0_splitters", "l0_max_sample_range",
+              "l0_max_light_bucket"]
 
 
 class SemisortError(RuntimeError):
@@ -70,6 +71,15 @@ def lib():
                 f.restype = i32
             L.semisort_equal_noalloc.argtypes = [i32, i32, vp, vp, vp, vp, u64, vp, vp]
             L.semisort_equal_noalloc.restype = i32
+            L.ss_mlp_workspace_size.argtypes = []
+            L.ss_mlp_workspace_size.restype = sz
+            L.ss_mlp_loss_grad.argtypes = [vp, vp, vp, ctypes.c_uint32, vp, vp, sz, vp]
+            L.ss_mlp_loss_grad.restype = i32
+            L.ss_mlp_train.argtypes = [vp, vp, ctypes.c_uint32, vp, ctypes.c_uint32, ctypes.c_float, vp, vp, vp, sz,
+                                       vp]
+            L.ss_mlp_train.restype = i32
+            L.ss_mlp_invert.argtypes = [vp, i32, u64, u64, ctypes.c_uint32, vp, vp, sz, vp]
+            L.ss_mlp_invert.restype = i32
             L.collect_reduce.argtypes = [i32, vp, vp, vp, vp, u64, vp, u64, vp, sz, vp, vp]
             L.collect_reduce.restype = i32
             L.histogram.argtypes = [i32, vp, vp, vp, u64, vp, u64, vp, sz, vp, vp]
@@ -257,3 +267,44 @@ def hash_u64(keys, salt: int, stream=None):
     _check(lib().ss_hash_u64(_ptr(keys), _ptr(out), keys.numel(), salt & 0xFFFFFFFFFFFFFFFF, _stream(stream)),
            "ss_hash_u64")
     return out
+
+
+MLP_PARAMS = 1153
+
+
+def _mlp_ws(device):
+    torch = _torch()
+    return torch.empty(int(lib().ss_mlp_workspace_size()), dtype=torch.uint8, device=device)
+
+
+def mlp_loss_grad(params, x, t, stream=None):
+    """(loss, gradient) of the learned-splitter model on points (x, t); float32 device tensors."""
+    torch = _torch()
+    out = torch.empty(MLP_PARAMS + 1, dtype=torch.float32, device=params.device)
+    ws = _mlp_ws(params.device)
+    _check(lib().ss_mlp_loss_grad(_ptr(params), _ptr(x), _ptr(t), x.numel(), _ptr(out), _ptr(ws), ws.numel(),
+                                  _stream(stream)), "ss_mlp_loss_grad")
+    return out[MLP_PARAMS], out[:MLP_PARAMS]
+
+
+def mlp_train(x, t, params0, steps, lr, stream=None):
+    """Trained parameters and the loss at them (float32 device tensors)."""
+    torch = _torch()
+    p = torch.empty(MLP_PARAMS, dtype=torch.float32, device=params0.device)
+    loss = torch.empty(1, dtype=torch.float32, device=params0.device)
+    ws = _mlp_ws(params0.device)
+    _check(lib().ss_mlp_train(_ptr(x), _ptr(t), x.numel(), _ptr(params0), steps, float(lr), _ptr(p), _ptr(loss),
+                              _ptr(ws), ws.numel(), _stream(stream)), "ss_mlp_train")
+    return p, loss
+
+
+def mlp_invert(params, key_type, kmin, kmax, n_light_log2, stream=None):
+    """The 2^n_light_log2 - 1 integer splitters of the model over [kmin, kmax]."""
+    torch = _torch()
+    nl = 1 << n_light_log2
+    out = torch.empty(nl - 1, dtype=torch.uint32 if key_type == SS_U32 else torch.uint64, device=params.device)
+    ws = _mlp_ws(params.device)
+    _check(lib().ss_mlp_invert(_ptr(params), key_type, kmin, kmax, n_light_log2, _ptr(out), _ptr(ws), ws.numel(),
+                               _stream(stream)), "ss_mlp_invert")
+    return out
+

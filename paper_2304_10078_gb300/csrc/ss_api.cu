@@ -10,6 +10,7 @@
 #include "../../include/semisort.h"
 #include "ss_common.cuh"
 #include "ss_host.h"
+#include "ss_learn.cuh"
 #include "ss_plan.h"
 
 using namespace ss;
@@ -158,6 +159,8 @@ ss_status make_plan(int op, int kt, int vt, uint64_t n, const ss_options* opt, i
   o = al(o + (wide && multi ? (size_t)kBigSample * P->kbytes : 0));
   P->off_bigs_tmp = o;
   o = al(o + (wide && multi ? (size_t)kBigSample * P->kbytes : 0));
+  P->off_learn = o;
+  o = al(o + (wide && multi ? sizeof(LearnState) : 0));
   P->off_ctrl = 0;
   P->total = o;
   return SS_OK;
@@ -201,6 +204,7 @@ void fill_work(const Plan& P, void* ws, Work* w) {
   w->scratch32 = reinterpret_cast<uint32_t*>(b + P.off_scratch32);
   w->bigs = b + P.off_bigs;
   w->bigs_tmp = b + P.off_bigs_tmp;
+  w->learn = b + P.off_learn;
   w->ctrl = reinterpret_cast<Ctrl*>(b + P.off_ctrl);
 }
 
@@ -266,6 +270,7 @@ ss_status semisort_common(int op, ss_type kt, ss_type vt, const void* keys, cons
     if (overlap(rk, rv) || overlap(rk, rvo) || overlap(rko, rv) || overlap(rko, rvo)) return SS_ERR_INVALID_ARG;
     if ((keys == keys_out) != (vals == vals_out)) return SS_ERR_INVALID_ARG;
   }
+  if (opt && (opt->splitter_mode < 0 || opt->splitter_mode > 1)) return SS_ERR_INVALID_ARG;
   Work w;
   memset(&w, 0, sizeof(w));
   fill_work(P, ws, &w);
@@ -275,6 +280,7 @@ ss_status semisort_common(int op, ss_type kt, ss_type vt, const void* keys, cons
   w.out_k = keys_out;
   w.out_v = vals_out;
   w.has_vals = vals != nullptr;
+  w.splitter_mode = (op == kOpLess && opt) ? (uint32_t)opt->splitter_mode : 0u;
   cudaStream_t st = reinterpret_cast<cudaStream_t>(stream);
   PhaseTimer* tm = timer_for(opt, st);
   cudaError_t e = dispatch(op, kt, vals ? (int)vt : 2, P, w, st, tm);
@@ -403,7 +409,7 @@ int ss_get_stats(void* ws, ss_stream_t stream, uint64_t* out, int count) {
   Ctrl h;
   if (cudaMemcpyAsync(&h, ws, sizeof(Ctrl), cudaMemcpyDeviceToHost, st) != cudaSuccess) return 0;
   if (cudaStreamSynchronize(st) != cudaSuccess) return 0;
-  const int m = std::min(count, 12);
+  const int m = std::min(count, 14);
   for (int i = 0; i < m; ++i) out[i] = h.stats[i];
   return m;
 }
@@ -499,4 +505,85 @@ extern "C" ss_status semisort_equal_noalloc(ss_type key_type, ss_type val_type, 
   // resets the control block, and every other region is written before it is read.
   return semisort_common(kOpEqual, key_type, val_type, keys, vals, keys_out, vals_out, n, ws, kNoAllocBytes, &o,
                          stream);
+}
+
+// ---------------------------------------------------------------------------
+// The learned-splitter model on its own (test and inspection entry points).
+// ---------------------------------------------------------------------------
+extern "C" size_t ss_mlp_workspace_size(void) { return sizeof(LearnState); }
+
+namespace {
+
+ss_status mlp_setup(const float* d_params, const float* d_x, const float* d_t, uint32_t m, void* ws, size_t ws_bytes,
+                    cudaStream_t st, LearnState** out) {
+  if (!ws || !aligned16(ws) || ws_bytes < sizeof(LearnState)) return SS_ERR_WORKSPACE_TOO_SMALL;
+  if (m > (uint32_t)(kGradCTAsMax * kGradThreads)) return SS_ERR_UNSUPPORTED;
+  LearnState* L = reinterpret_cast<LearnState*>(ws);
+  if (d_params && cudaMemcpyAsync(L->p, d_params, sizeof(float) * kMlpParams, cudaMemcpyDeviceToDevice, st) != cudaSuccess)
+    return SS_ERR_CUDA;
+  if (m && (cudaMemcpyAsync(L->x, d_x, sizeof(float) * m, cudaMemcpyDeviceToDevice, st) != cudaSuccess ||
+            cudaMemcpyAsync(L->t, d_t, sizeof(float) * m, cudaMemcpyDeviceToDevice, st) != cudaSuccess))
+    return SS_ERR_CUDA;
+  if (cudaMemsetAsync(L->m, 0, sizeof(float) * 2 * kMlpParams, st) != cudaSuccess) return SS_ERR_CUDA;
+  *out = L;
+  return SS_OK;
+}
+
+}  // namespace
+
+extern "C" ss_status ss_mlp_loss_grad(const float* d_params, const float* d_x, const float* d_t, uint32_t m,
+                                      float* d_out, void* ws, size_t ws_bytes, ss_stream_t stream) {
+  if (!d_params || !d_x || !d_t || !d_out || m == 0) return SS_ERR_INVALID_ARG;
+  cudaStream_t st = reinterpret_cast<cudaStream_t>(stream);
+  LearnState* L = nullptr;
+  ss_status s = mlp_setup(d_params, d_x, d_t, m, ws, ws_bytes, st, &L);
+  if (s != SS_OK) return s;
+  k_learn_range<<<1, 32, 0, st>>>(L, 0, 1, m);
+  k_learn_step<<<(m + kGradThreads - 1) / kGradThreads, kGradThreads, 0, st>>>(L, 0, 0.0f);
+  if (cudaMemcpyAsync(d_out, L->grad, sizeof(float) * (kMlpParams + 1), cudaMemcpyDeviceToDevice, st) != cudaSuccess)
+    return SS_ERR_CUDA;
+  return cudaGetLastError() == cudaSuccess ? SS_OK : SS_ERR_CUDA;
+}
+
+extern "C" ss_status ss_mlp_train(const float* d_x, const float* d_t, uint32_t m, const float* d_params0,
+                                  uint32_t steps, float lr, float* d_params_out, float* d_loss_out, void* ws,
+                                  size_t ws_bytes, ss_stream_t stream) {
+  if (!d_x || !d_t || !d_params0 || !d_params_out || m == 0) return SS_ERR_INVALID_ARG;
+  cudaStream_t st = reinterpret_cast<cudaStream_t>(stream);
+  LearnState* L = nullptr;
+  ss_status s = mlp_setup(d_params0, d_x, d_t, m, ws, ws_bytes, st, &L);
+  if (s != SS_OK) return s;
+  k_learn_range<<<1, 32, 0, st>>>(L, 0, 1, m);
+  const uint32_t ctas = (m + kGradThreads - 1) / kGradThreads;
+  for (uint32_t i = 1; i <= steps; ++i) k_learn_step<<<ctas, kGradThreads, 0, st>>>(L, (int)i, lr);
+  k_learn_step<<<ctas, kGradThreads, 0, st>>>(L, 0, 0.0f);  // loss at the final parameters
+  if (cudaMemcpyAsync(d_params_out, L->p, sizeof(float) * kMlpParams, cudaMemcpyDeviceToDevice, st) != cudaSuccess)
+    return SS_ERR_CUDA;
+  if (d_loss_out &&
+      cudaMemcpyAsync(d_loss_out, &L->grad[kMlpParams], sizeof(float), cudaMemcpyDeviceToDevice, st) != cudaSuccess)
+    return SS_ERR_CUDA;
+  return cudaGetLastError() == cudaSuccess ? SS_OK : SS_ERR_CUDA;
+}
+
+extern "C" ss_status ss_mlp_invert(const float* d_params, ss_type key_type, uint64_t kmin, uint64_t kmax,
+                                   uint32_t n_light_log2, void* d_splitters, void* ws, size_t ws_bytes,
+                                   ss_stream_t stream) {
+  if (!d_params || !d_splitters || kmax < kmin) return SS_ERR_INVALID_ARG;
+  if (n_light_log2 < 1 || n_light_log2 > (uint32_t)kLessTopLog2) return SS_ERR_UNSUPPORTED;
+  if (key_type != SS_U32 && key_type != SS_U64) return SS_ERR_UNSUPPORTED;
+  if (key_type == SS_U32 && kmax > 0xFFFFFFFFull) return SS_ERR_INVALID_ARG;
+  cudaStream_t st = reinterpret_cast<cudaStream_t>(stream);
+  LearnState* L = nullptr;
+  ss_status s = mlp_setup(d_params, nullptr, nullptr, 0, ws, ws_bytes, st, &L);
+  if (s != SS_OK) return s;
+  k_learn_range<<<1, 32, 0, st>>>(L, kmin, kmax, 0);
+  const uint32_t nl = 1u << n_light_log2;
+  if (key_type == SS_U32)
+    k_learn_invert<uint32_t><<<(nl + 255) / 256, 256, 0, st>>>(L, nullptr, n_light_log2);
+  else
+    k_learn_invert<uint64_t><<<(nl + 255) / 256, 256, 0, st>>>(L, nullptr, n_light_log2);
+  const size_t kb = key_type == SS_U32 ? 4 : 8;
+  if (cudaMemcpyAsync(d_splitters, L->splitters, kb * (nl - 1), cudaMemcpyDeviceToDevice, st) != cudaSuccess)
+    return SS_ERR_CUDA;
+  return cudaGetLastError() == cudaSuccess ? SS_OK : SS_ERR_CUDA;
 }

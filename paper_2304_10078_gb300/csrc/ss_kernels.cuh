@@ -17,6 +17,7 @@
 #include <type_traits>
 
 #include "ss_common.cuh"
+#include "ss_learn.cuh"
 #include "ss_plan.h"
 
 namespace ss {
@@ -451,16 +452,33 @@ __global__ void __launch_bounds__(256) k_bigsample_merge(Work w) {
 }
 
 // Boundaries of the semisort_< top level from the sorted sample: n_L - 1
-// splitters at evenly spaced sample ranks (or, in learned mode, the integer
-// splitters the CDF model produced, see k_learn_*) merged with the heavy keys
-// -- keys whose sample run reaches the expected size of one range bucket,
-// at most kMaxHeavy of them in key order -- into one sorted list with a flag
-// per heavy key (equality buckets, as in k_sample).  One CTA.
+// candidate splitters -- keys at evenly spaced sample ranks, or, in learned
+// mode, the integer splitters inverted from the CDF model -- merged with the
+// heavy keys (keys whose sample run reaches the expected size of one range
+// bucket, at most min(n_L, 512) of them in key order) into one sorted list with
+// a flag per heavy key (equality buckets, as in k_sample).  Learned splitters
+// are judged on the sample: if any range bucket would hold more than twice its
+// share of the (non-heavy) sample, the sampled splitters are used instead.
+// stats[11]: 0 sampled, 1 learned, 2 learned rejected; stats[12]: the largest
+// range bucket's sample count.  One CTA.
 template <class K>
-__global__ void __launch_bounds__(1024) k_less_split(Work w, const K* learned) {
+__device__ __forceinline__ uint32_t sample_lower(const K* S, const K& k, bool upper) {
+  uint32_t lo = 0, hi = kBigSample;
+  while (lo < hi) {
+    const uint32_t mid = (lo + hi) >> 1;
+    if (upper ? !KeyT<K>::lt(k, S[mid]) : KeyT<K>::lt(S[mid], k))
+      lo = mid + 1;
+    else
+      hi = mid;
+  }
+  return lo;
+}
+
+template <class K>
+__global__ void __launch_bounds__(1024) k_less_split(Work w, const LearnState* L) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
   __shared__ uint32_t tmp[33];
-  __shared__ uint32_t nh_sh;
+  __shared__ uint32_t nh_sh, q_sh, maxc_sh;
   Seg* sgp = w.segs[0];
   if (w.ctrl->nsegs[0] == 0 || sgp[0].lbits == 0) return;
   const uint32_t nl = 1u << sgp[0].lbits;
@@ -470,8 +488,10 @@ __global__ void __launch_bounds__(1024) k_less_split(Work w, const K* learned) {
   if (tau < 2) tau = 2;
   K* cs = reinterpret_cast<K*>(smem_raw);  // n_L - 1 candidate splitters
   K* hs = cs + nl;                         // heavy keys (at most hcap)
-  for (uint32_t j = 1 + threadIdx.x; j < nl; j += blockDim.x)
-    cs[j - 1] = learned ? learned[j - 1] : S[(uint64_t)j * kBigSample / nl];
+  K* bs = hs + kMaxHeavy;                  // merged boundaries (< 2 n_L)
+  uint16_t* fs = reinterpret_cast<uint16_t*>(bs + 2 * nl);
+  bool learned = L != nullptr && L->usable;
+  // heavy keys
   if (threadIdx.x == 0) nh_sh = 0;
   __syncthreads();
   for (uint32_t t0 = 0; t0 < kBigSample; t0 += blockDim.x) {
@@ -488,41 +508,83 @@ __global__ void __launch_bounds__(1024) k_less_split(Work w, const K* learned) {
     __syncthreads();
   }
   const uint32_t nh = nh_sh < hcap ? nh_sh : hcap;
-  if (threadIdx.x == 0) {
-    // q <= (n_L - 1) + hcap < 2 n_L boundaries: within the segment's 4 n_L rows
-    K* bnd = reinterpret_cast<K*>(w.splitters[0]) + sgp[0].bbase;
-    uint16_t* fl = w.htab[0] + 2ull * sgp[0].bbase;
-    uint32_t q = 0, j = 0, hi = 0;
-    bool have_last = false;
-    K last = cs[0];
-    while (j + 1 < nl || hi < nh) {
-      K c;
-      bool heavy;
-      if (j + 1 < nl && (hi >= nh || KeyT<K>::lt(cs[j], hs[hi]))) {
-        c = cs[j++];
-        heavy = false;
-      } else if (j + 1 < nl && KeyT<K>::eq(cs[j], hs[hi])) {
-        c = hs[hi++];
-        ++j;
-        heavy = true;
-      } else {
-        c = hs[hi++];
-        heavy = true;
+  for (int attempt = 0; attempt < 2; ++attempt) {
+    for (uint32_t j = 1 + threadIdx.x; j < nl; j += blockDim.x)
+      cs[j - 1] = learned ? reinterpret_cast<const K*>(L->splitters)[j - 1] : S[(uint64_t)j * kBigSample / nl];
+    __syncthreads();
+    if (threadIdx.x == 0) {
+      if (learned)  // the bisection in FP32 may step back by a rounding: make the list non-decreasing
+        for (uint32_t j = 1; j + 1 < nl; ++j)
+          if (KeyT<K>::lt(cs[j], cs[j - 1])) cs[j] = cs[j - 1];
+      // q <= (n_L - 1) + hcap < 2 n_L boundaries
+      uint32_t q = 0, j = 0, hi = 0;
+      bool have_last = false;
+      K last = cs[0];
+      while (j + 1 < nl || hi < nh) {
+        K c;
+        bool heavy;
+        if (j + 1 < nl && (hi >= nh || KeyT<K>::lt(cs[j], hs[hi]))) {
+          c = cs[j++];
+          heavy = false;
+        } else if (j + 1 < nl && KeyT<K>::eq(cs[j], hs[hi])) {
+          c = hs[hi++];
+          ++j;
+          heavy = true;
+        } else {
+          c = hs[hi++];
+          heavy = true;
+        }
+        if (have_last && KeyT<K>::eq(c, last)) {
+          if (heavy) fs[q - 1] = 1;
+          continue;
+        }
+        bs[q] = c;
+        fs[q] = heavy ? 1 : 0;
+        ++q;
+        last = c;
+        have_last = true;
       }
-      if (have_last && KeyT<K>::eq(c, last)) {
-        if (heavy) fl[q - 1] = 1;
-        continue;
-      }
-      bnd[q] = c;
-      fl[q] = heavy ? 1 : 0;
-      ++q;
-      last = c;
-      have_last = true;
+      q_sh = q;
+      maxc_sh = 0;
     }
+    __syncthreads();
+    const uint32_t q = q_sh;
+    // sample count of every range bucket u (keys between boundaries u-1 and u)
+    uint32_t mx = 0;
+    for (uint32_t u = threadIdx.x; u <= q; u += blockDim.x) {
+      const uint32_t lo = u == 0 ? 0u : sample_lower<K>(S, bs[u - 1], fs[u - 1] != 0);
+      const uint32_t hi = u == q ? kBigSample : sample_lower<K>(S, bs[u], false);
+      const uint32_t c = hi > lo ? hi - lo : 0u;
+      mx = c > mx ? c : mx;
+    }
+    atomicMax(&maxc_sh, mx);
+    __syncthreads();
+    const bool reject = learned && maxc_sh > 2 * (kBigSample / nl);
+    if (!reject) break;
+    learned = false;  // fall back to the sampled splitters
+    __syncthreads();
+  }
+  const uint32_t q = q_sh;
+  K* bnd = reinterpret_cast<K*>(w.splitters[0]) + sgp[0].bbase;
+  uint16_t* fl = w.htab[0] + 2ull * sgp[0].bbase;
+  for (uint32_t u = threadIdx.x; u < q; u += blockDim.x) {
+    bnd[u] = bs[u];
+    fl[u] = fs[u];
+  }
+  if (threadIdx.x == 0) {
     sgp[0].nh = q;
     sgp[0].nb = 2 * q + 1;
     w.ctrl->stats[7] = nh;
+    w.ctrl->stats[11] = L == nullptr ? 0u : learned ? 1u : 2u;
+    w.ctrl->stats[12] = maxc_sh;
   }
+}
+
+// Shared memory of k_less_split for keys of type K.
+template <class K>
+constexpr size_t less_split_smem() {
+  return ((size_t)(1u << kLessTopLog2) + kMaxHeavy + 2 * (1u << kLessTopLog2)) * sizeof(K) +
+         2 * (1u << kLessTopLog2) * sizeof(uint16_t);
 }
 
 // Load a segment's heavy keys and table (semisort_<: boundaries and flags)
@@ -752,11 +814,12 @@ __global__ void __launch_bounds__(1024) k_scan(Work w, LevelBufs lb) {
     __syncthreads();
     if (threadIdx.x == 0) carry = 0;
     __syncthreads();
-    uint32_t nfin = 0, nnext = 0;
+    uint32_t nfin = 0, nnext = 0, lmax = 0;
     for (uint32_t b0 = 0; b0 < nb; b0 += blockDim.x) {
       const uint32_t b = b0 + threadIdx.x;
       const uint32_t sz = b < nb ? bsize[b] : 0;
       const bool heavy = is_heavy<OP>(b, nl);
+      if (!heavy && sz > lmax) lmax = sz;
       // Collect-reduce and histogram never move heavy records (Sec. 3.5).
       const uint32_t lay = (heavy && (OP == kOpReduce || OP == kOpHist)) ? 0 : sz;
       uint32_t tot;
@@ -774,6 +837,7 @@ __global__ void __launch_bounds__(1024) k_scan(Work w, LevelBufs lb) {
     }
     const uint32_t tf = block_reduce_sum(nfin, tmp);
     const uint32_t tn = block_reduce_sum(nnext, tmp);
+    if (lb.level == 0) atomicMax((unsigned long long*)&w.ctrl->stats[13], (unsigned long long)lmax);
     if (threadIdx.x == 0) {
       const uint32_t nw = refine_windows<OP>(szs, boff, nl, nb, w.alpha, last_level, sg.start, lb.dst_id,
                                              lb.level, nullptr, 0, 0);

@@ -65,7 +65,7 @@ cudaError_t launch_pipeline(const Plan& P, const Work& w, cudaStream_t st, const
   if ((e = set_smem(k_count<K, V, OP, false>, count_smem)) != cudaSuccess) return e;
   if ((e = set_smem(k_count<K, V, OP, kWide>, count_smem_top)) != cudaSuccess) return e;
   const size_t bigs_smem = (size_t)BigRun<K>::len * sizeof(K);
-  const size_t split_smem = ((size_t)(1u << kLessTopLog2) + kMaxHeavy) * sizeof(K);
+  const size_t split_smem = less_split_smem<K>();
   if constexpr (kWide) {
     if ((e = set_smem(k_bigsample_sort<K>, bigs_smem)) != cudaSuccess) return e;
     if ((e = set_smem(k_less_split<K>, split_smem)) != cudaSuccess) return e;
@@ -97,10 +97,24 @@ cudaError_t launch_pipeline(const Plan& P, const Work& w, cudaStream_t st, const
       k_plan<OP><<<1, 1024, 0, st>>>(w, level);
       if (tm) tm->mark(level == 0 ? "plan.L0" : "plan.L1+");
       if (top_wide) {
+        if constexpr (kWide) {
         k_bigsample_sort<K><<<BigRun<K>::runs, 1024, bigs_smem, st>>>(w);
         k_bigsample_merge<K><<<kBigSample / 256, 256, 0, st>>>(w);
-        k_less_split<K><<<1, 1024, split_smem, st>>>(w, nullptr);
-        nl += 3;
+        nl += 2;
+        LearnState* ls = nullptr;
+        if (w.splitter_mode == 1) {
+          // learned splitters: fit the CDF model to the sorted sample, invert it
+          ls = reinterpret_cast<LearnState*>(w.learn);
+          k_learn_prep<K><<<1, 1024, 0, st>>>(reinterpret_cast<const K*>(w.bigs), ls, w.seed);
+          for (int s = 1; s <= kLearnSteps; ++s)
+            k_learn_step<<<kLearnPts / kGradThreads, kGradThreads, 0, st>>>(ls, s, kLearnLr);
+          k_learn_invert<K><<<((1u << kLessTopLog2) + 255) / 256, 256, 0, st>>>(ls, w.segs[0], 0);
+          nl += kLearnSteps + 2;
+          if (tm) tm->mark("learn.L0");
+        }
+        k_less_split<K><<<1, 1024, split_smem, st>>>(w, ls);
+        ++nl;
+        }
       } else {
         const uint32_t s_cap = level == 0 ? P.s1 : P.s2;
         k_sample<K, V, OP><<<cap(segs, nsm * 2), 1024, (size_t)s_cap * sizeof(K), st>>>(w, lb, s_cap);

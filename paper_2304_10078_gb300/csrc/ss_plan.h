@@ -123,6 +123,8 @@ struct Work {
   void* splitters[kMaxLevels];  // semisort_<: per-segment sorted boundaries at bbase
   void* bigs;           // semisort_<: the sorted top-level sample (kBigSample keys)
   void* bigs_tmp;       // its sorted runs before the merge
+  void* learn;          // semisort_<: learned-splitter state (LearnState)
+  uint32_t splitter_mode;  // 0 sampled, 1 learned (semisort_< top level)
   uint32_t* scratch32;  // histogram: per-position counts of compacted base cases
   uint64_t* item_aux;   // collect-reduce: heavy totals per item
   uint64_t out_capacity;
@@ -142,7 +144,7 @@ struct Plan {
       off_htab[kMaxLevels], off_bsize[kMaxLevels], off_boff[kMaxLevels], off_hpart[kMaxLevels],
       off_split[kMaxLevels];
   size_t off_items, off_item_out, off_item_pos, off_block_sums, off_ctrl, off_scratch32, off_item_aux;
-  size_t off_bigs, off_bigs_tmp;
+  size_t off_bigs, off_bigs_tmp, off_learn;
   size_t total;
 };
 
