@@ -184,6 +184,49 @@ ss_status ss_mlp_invert(const float* d_params, ss_type key_type, uint64_t kmin, 
                         uint32_t n_light_log2, void* d_splitters, void* ws, size_t ws_bytes,
                         ss_stream_t stream);
 
+/* Batched forms: num_instances independent problems over one concatenation of
+ * records.  d_offsets (device, num_instances + 1 entries) gives instance i the
+ * records [d_offsets[i], d_offsets[i+1]); it must start at 0, end at n and not
+ * decrease (otherwise the device flag reports SS_ERR_INVALID_ARG and nothing is
+ * written).  All instances run in one pipeline: instances of at most alpha
+ * records go straight to the base case, larger ones become the top level's
+ * segments, so one call enqueues the same fixed kernel sequence whatever the
+ * instance sizes (and can be captured in a CUDA graph).  Workspace:
+ * ss_workspace_size_batched().  options.splitter_mode is ignored (sampled
+ * splitters); options.subarray also sets the top level's subarray size
+ * (default 2^18 records). */
+ss_status ss_workspace_size_batched(int op, ss_type key_type, ss_type val_type, uint64_t n,
+                                    uint32_t num_instances, const ss_options* opt, size_t* bytes);
+
+/* semisort_= of every instance within its own range of keys_out/vals_out. */
+ss_status semisort_equal_batched(ss_type key_type, ss_type val_type, const void* keys, const void* vals,
+                                 void* keys_out, void* vals_out, const uint64_t* d_offsets,
+                                 uint32_t num_instances, uint64_t n, void* ws, size_t ws_bytes,
+                                 const ss_options* opt, ss_stream_t stream);
+
+/* semisort_< (stable sort by key) of every instance within its own range. */
+ss_status semisort_less_batched(ss_type key_type, ss_type val_type, const void* keys, const void* vals,
+                                void* keys_out, void* vals_out, const uint64_t* d_offsets,
+                                uint32_t num_instances, uint64_t n, void* ws, size_t ws_bytes,
+                                const ss_options* opt, ss_stream_t stream);
+
+/* collect-reduce of every instance: instance i's (unique key, sum) pairs occupy
+ * ukeys_out/sums_out[d_out_offsets[i] .. d_out_offsets[i+1]) (device, num_instances
+ * + 1 entries) and d_num_unique[i] (device, num_instances entries) is their number.
+ * capacity bounds the total; beyond it nothing is stored and the device flag
+ * reports SS_ERR_CAPACITY (the counts and offsets are still written). */
+ss_status collect_reduce_batched(ss_type key_type, const void* keys, const uint64_t* vals,
+                                 const uint64_t* d_offsets, uint32_t num_instances, uint64_t n,
+                                 void* ukeys_out, uint64_t* sums_out, uint64_t capacity,
+                                 uint64_t* d_num_unique, uint64_t* d_out_offsets, void* ws,
+                                 size_t ws_bytes, const ss_options* opt, ss_stream_t stream);
+
+/* histogram of every instance, laid out as collect_reduce_batched. */
+ss_status histogram_batched(ss_type key_type, const void* keys, const uint64_t* d_offsets,
+                            uint32_t num_instances, uint64_t n, void* ukeys_out, uint32_t* counts_out,
+                            uint64_t capacity, uint64_t* d_num_unique, uint64_t* d_out_offsets, void* ws,
+                            size_t ws_bytes, const ss_options* opt, ss_stream_t stream);
+
 /* Reads (and clears) the device error flag left in `ws` by earlier calls on
  * `stream`; synchronizes the stream.  *code receives the ss_status of the
  * first device-side failure (SS_OK if none). */

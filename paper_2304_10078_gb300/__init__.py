@@ -80,6 +80,17 @@ def lib():
             L.ss_mlp_train.restype = i32
             L.ss_mlp_invert.argtypes = [vp, i32, u64, u64, ctypes.c_uint32, vp, vp, sz, vp]
             L.ss_mlp_invert.restype = i32
+            L.ss_workspace_size_batched.argtypes = [i32, i32, i32, u64, ctypes.c_uint32, vp, ctypes.POINTER(sz)]
+            L.ss_workspace_size_batched.restype = i32
+            for name in ("semisort_equal_batched", "semisort_less_batched"):
+                f = getattr(L, name)
+                f.argtypes = [i32, i32, vp, vp, vp, vp, vp, ctypes.c_uint32, u64, vp, sz, vp, vp]
+                f.restype = i32
+            L.collect_reduce_batched.argtypes = [i32, vp, vp, vp, ctypes.c_uint32, u64, vp, vp, u64, vp, vp, vp, sz,
+                                                 vp, vp]
+            L.collect_reduce_batched.restype = i32
+            L.histogram_batched.argtypes = [i32, vp, vp, ctypes.c_uint32, u64, vp, vp, u64, vp, vp, vp, sz, vp, vp]
+            L.histogram_batched.restype = i32
             L.collect_reduce.argtypes = [i32, vp, vp, vp, vp, u64, vp, u64, vp, sz, vp, vp]
             L.collect_reduce.restype = i32
             L.histogram.argtypes = [i32, vp, vp, vp, u64, vp, u64, vp, sz, vp, vp]
@@ -307,4 +318,91 @@ def mlp_invert(params, key_type, kmin, kmax, n_light_log2, stream=None):
     _check(lib().ss_mlp_invert(_ptr(params), key_type, kmin, kmax, n_light_log2, _ptr(out), _ptr(ws), ws.numel(),
                                _stream(stream)), "ss_mlp_invert")
     return out
+
+
+def workspace_size_batched(op: int, kcode: int, vcode: int, n: int, num_instances: int,
+                           options: Options | None = None) -> int:
+    out = ctypes.c_size_t(0)
+    _check(lib().ss_workspace_size_batched(op, kcode, vcode, n, num_instances, _opt_ptr(options), ctypes.byref(out)),
+           "ss_workspace_size_batched")
+    return out.value
+
+
+def alloc_workspace_batched(op: int, keys, offsets, vals=None, options: Options | None = None):
+    torch = _torch()
+    nbytes = workspace_size_batched(op, key_code(keys), val_code(vals), keys.shape[0], offsets.numel() - 1, options)
+    return torch.empty(max(nbytes, 256), dtype=torch.uint8, device=keys.device)
+
+
+def _semisort_batched(fn, op, keys, vals, offsets, keys_out, vals_out, workspace, options, stream):
+    torch = _torch()
+    if keys_out is None:
+        keys_out = torch.empty_like(keys)
+    if vals is not None and vals_out is None:
+        vals_out = torch.empty_like(vals)
+    if workspace is None:
+        workspace = alloc_workspace_batched(op, keys, offsets, vals, options)
+    code = fn(key_code(keys), val_code(vals), _ptr(keys), _ptr(vals), _ptr(keys_out), _ptr(vals_out), _ptr(offsets),
+              offsets.numel() - 1, keys.shape[0], _ptr(workspace), workspace.numel(), _opt_ptr(options),
+              _stream(stream))
+    _check(code, fn.__name__)
+    return keys_out, vals_out
+
+
+def semisort_equal_batched(keys, vals, offsets, keys_out=None, vals_out=None, workspace=None, options=None,
+                           stream=None):
+    """semisort_= of every instance [offsets[i], offsets[i+1]) (offsets: uint64 device tensor)."""
+    return _semisort_batched(lib().semisort_equal_batched, OP_EQUAL, keys, vals, offsets, keys_out, vals_out,
+                             workspace, options, stream)
+
+
+def semisort_less_batched(keys, vals, offsets, keys_out=None, vals_out=None, workspace=None, options=None,
+                          stream=None):
+    """semisort_< (stable sort) of every instance."""
+    return _semisort_batched(lib().semisort_less_batched, OP_LESS, keys, vals, offsets, keys_out, vals_out,
+                             workspace, options, stream)
+
+
+def collect_reduce_batched(keys, vals, offsets, capacity=None, ukeys_out=None, sums_out=None, num_unique=None,
+                           out_offsets=None, workspace=None, options=None, stream=None):
+    """Per-instance (unique keys, sums): returns (ukeys, sums, num_unique[I], out_offsets[I+1])."""
+    torch = _torch()
+    n = keys.shape[0]
+    ni = offsets.numel() - 1
+    cap = n if capacity is None else capacity
+    dev = keys.device
+    ukeys_out = torch.empty((cap,) + tuple(keys.shape[1:]), dtype=keys.dtype, device=dev) if ukeys_out is None \
+        else ukeys_out
+    sums_out = torch.empty(cap, dtype=torch.uint64, device=dev) if sums_out is None else sums_out
+    num_unique = torch.zeros(ni, dtype=torch.uint64, device=dev) if num_unique is None else num_unique
+    out_offsets = torch.zeros(ni + 1, dtype=torch.uint64, device=dev) if out_offsets is None else out_offsets
+    if workspace is None:
+        workspace = alloc_workspace_batched(OP_REDUCE, keys, offsets, vals, options)
+    code = lib().collect_reduce_batched(key_code(keys), _ptr(keys), _ptr(vals), _ptr(offsets), ni, n,
+                                        _ptr(ukeys_out), _ptr(sums_out), cap, _ptr(num_unique), _ptr(out_offsets),
+                                        _ptr(workspace), workspace.numel(), _opt_ptr(options), _stream(stream))
+    _check(code, "collect_reduce_batched")
+    return ukeys_out, sums_out, num_unique, out_offsets
+
+
+def histogram_batched(keys, offsets, capacity=None, ukeys_out=None, counts_out=None, num_unique=None,
+                      out_offsets=None, workspace=None, options=None, stream=None):
+    """Per-instance (unique keys, counts): returns (ukeys, counts, num_unique[I], out_offsets[I+1])."""
+    torch = _torch()
+    n = keys.shape[0]
+    ni = offsets.numel() - 1
+    cap = n if capacity is None else capacity
+    dev = keys.device
+    ukeys_out = torch.empty((cap,) + tuple(keys.shape[1:]), dtype=keys.dtype, device=dev) if ukeys_out is None \
+        else ukeys_out
+    counts_out = torch.empty(cap, dtype=torch.uint32, device=dev) if counts_out is None else counts_out
+    num_unique = torch.zeros(ni, dtype=torch.uint64, device=dev) if num_unique is None else num_unique
+    out_offsets = torch.zeros(ni + 1, dtype=torch.uint64, device=dev) if out_offsets is None else out_offsets
+    if workspace is None:
+        workspace = alloc_workspace_batched(OP_HIST, keys, offsets, None, options)
+    code = lib().histogram_batched(key_code(keys), _ptr(keys), _ptr(offsets), ni, n, _ptr(ukeys_out),
+                                   _ptr(counts_out), cap, _ptr(num_unique), _ptr(out_offsets), _ptr(workspace),
+                                   workspace.numel(), _opt_ptr(options), _stream(stream))
+    _check(code, "histogram_batched")
+    return ukeys_out, counts_out, num_unique, out_offsets
 

@@ -40,8 +40,11 @@ int num_sms() {
 int kbytes_of(int t) { return t == SS_U32 ? 4 : t == SS_U64 ? 8 : t == SS_U128 ? 16 : 0; }
 
 // Capacities of every device work list for n records (see ss_plan.h).
-ss_status make_plan(int op, int kt, int vt, uint64_t n, const ss_options* opt, int nsm, Plan* P) {
+ss_status make_plan(int op, int kt, int vt, uint64_t n, const ss_options* opt, int nsm, Plan* P,
+                    uint32_t num_inst = 0) {
   memset(P, 0, sizeof(*P));
+  const bool batched = num_inst > 0;
+  P->num_inst = num_inst;
   P->n = n;
   P->op = op;
   P->kbytes = kbytes_of(kt);
@@ -57,7 +60,7 @@ ss_status make_plan(int op, int kt, int vt, uint64_t n, const ss_options* opt, i
   // top-level light buckets: n_L ~ 2n / alpha, at most 2^9 hash buckets or 2^11
   // semisort_< key ranges
   // (semisort_< with 16-byte keys keeps the narrow top level: 2^8 ranges)
-  const bool wide = op == SS_OP_SEMISORT_LESS && P->kbytes < 16;
+  const bool wide = op == SS_OP_SEMISORT_LESS && P->kbytes < 16 && !batched;
   const uint32_t lb_max = wide ? (uint32_t)kLessTopLog2
                                : op == SS_OP_SEMISORT_LESS ? (uint32_t)kMaxLightLog2 - 1 : (uint32_t)kMaxLightLog2;
   uint32_t lb1 = 0;
@@ -73,6 +76,8 @@ ss_status make_plan(int op, int kt, int vt, uint64_t n, const ss_options* opt, i
   uint32_t l2 = (opt && opt->subarray) ? opt->subarray : 32768;
   l2 = std::max<uint32_t>(((l2 + 4095) / 4096) * 4096, 4096);
   P->l2 = l2;
+  // batched calls: subarrays of `subarray` records (default 2^18) at level 0 too
+  if (batched) P->l1 = (opt && opt->subarray) ? l2 : (1u << 18);
   uint32_t s1 = (opt && opt->sample_size) ? opt->sample_size : 16384;
   uint32_t p2 = 2048;
   while (p2 < s1 && p2 < 16384) p2 <<= 1;
@@ -90,6 +95,14 @@ ss_status make_plan(int op, int kt, int vt, uint64_t n, const ss_options* opt, i
   P->tile_cap[0] = (uint32_t)((n + P->l1 - 1) / P->l1);
   P->bucket_cap[0] = rows0;
   P->c_cap[0] = (uint64_t)rows0 * P->tile_cap[0];
+  if (batched) {
+    // one segment per instance above alpha; each has n_L < 4m/alpha + 2 and at
+    // most 2 n_L (4 n_L for semisort_<) bucket rows, and m/l + 1 subarrays
+    P->seg_cap[0] = num_inst;
+    P->tile_cap[0] = (uint32_t)((n + P->l1 - 1) / P->l1 + num_inst);
+    P->bucket_cap[0] = (uint32_t)((less ? 16 : 8) * n / alpha + 8ull * num_inst + 64);
+    P->c_cap[0] = (uint64_t)kMaxBuckets * P->tile_cap[0];
+  }
   for (int l = 1; l < kMaxLevels; ++l) {
     const uint64_t segs = n / (alpha + 1) + 1;
     P->seg_cap[l] = (uint32_t)segs;
@@ -101,14 +114,14 @@ ss_status make_plan(int op, int kt, int vt, uint64_t n, const ss_options* opt, i
     // rows x subarrays: sum over segments of rows * (m/l2 + 1)
     P->c_cap[l] = (uint64_t)kMaxBuckets * ((n + l2 - 1) / l2) + P->bucket_cap[l];
   }
-  uint64_t items = n / kCopyChunk + 16;
+  uint64_t items = n / kCopyChunk + 16 + num_inst;
   for (int l = 0; l < kMaxLevels; ++l) items += P->bucket_cap[l];
   P->item_cap = (uint32_t)std::min<uint64_t>(items, 0xFFFFFFF0ull);
   // layout: control block first, so status calls can find it without a plan
   size_t o = al(sizeof(Ctrl));
   // temporaries T and T2 hold records (key, value) as array of structures;
   // collect-reduce / histogram always need T (compacted base-case outputs)
-  const bool multi = n > alpha;
+  const bool multi = n > alpha;  // (batched: some instance may exceed alpha)
   const bool need_t = multi || red;
   const size_t ralign = std::max(P->kbytes == 16 ? 16 : P->kbytes, P->vbytes);
   const size_t recbytes = (P->kbytes + P->vbytes + ralign - 1) / ralign * ralign;
@@ -142,7 +155,7 @@ ss_status make_plan(int op, int kt, int vt, uint64_t n, const ss_options* opt, i
     P->off_split[l] = o;
     o = al(o + (less ? (size_t)P->bucket_cap[l] * P->kbytes : 0));
   }
-  if (!multi) P->item_cap = 1;
+  if (!multi) P->item_cap = std::max<uint32_t>(1, num_inst);
   P->off_items = o;
   o = al(o + (size_t)P->item_cap * sizeof(Item));
   P->off_item_out = o;
@@ -161,6 +174,10 @@ ss_status make_plan(int op, int kt, int vt, uint64_t n, const ss_options* opt, i
   o = al(o + (wide && multi ? (size_t)kBigSample * P->kbytes : 0));
   P->off_learn = o;
   o = al(o + (wide && multi ? sizeof(LearnState) : 0));
+  P->off_inst_base = o;
+  o = al(o + (batched && red ? (size_t)5 * num_inst * 8 : 0));
+  P->off_inst_first = o;
+  o = al(o + (batched && red ? (size_t)5 * num_inst * 8 : 0));
   P->off_ctrl = 0;
   P->total = o;
   return SS_OK;
@@ -205,6 +222,9 @@ void fill_work(const Plan& P, void* ws, Work* w) {
   w->bigs = b + P.off_bigs;
   w->bigs_tmp = b + P.off_bigs_tmp;
   w->learn = b + P.off_learn;
+  w->inst_base = reinterpret_cast<uint64_t*>(b + P.off_inst_base);
+  w->inst_first = reinterpret_cast<uint64_t*>(b + P.off_inst_first);
+  w->num_inst = P.num_inst > 0 ? P.num_inst : 1;
   w->ctrl = reinterpret_cast<Ctrl*>(b + P.off_ctrl);
 }
 
@@ -247,7 +267,9 @@ cudaError_t dispatch(int op, int kt, int vt, const Plan& P, const Work& w, cudaS
 
 ss_status semisort_common(int op, ss_type kt, ss_type vt, const void* keys, const void* vals,
                           void* keys_out, void* vals_out, uint64_t n, void* ws, size_t ws_bytes,
-                          const ss_options* opt, ss_stream_t stream) {
+                          const ss_options* opt, ss_stream_t stream, const uint64_t* d_offsets = nullptr,
+                          uint32_t num_inst = 0) {
+  if (num_inst > 0 && !d_offsets) return SS_ERR_INVALID_ARG;
   if (n == 0) return SS_OK;
   if (!keys || !keys_out || !ws) return SS_ERR_INVALID_ARG;
   if ((vals == nullptr) != (vals_out == nullptr)) return SS_ERR_INVALID_ARG;
@@ -255,7 +277,7 @@ ss_status semisort_common(int op, ss_type kt, ss_type vt, const void* keys, cons
       (vals_out && !aligned16(vals_out)))
     return SS_ERR_INVALID_ARG;
   Plan P;
-  ss_status s = make_plan(op, kt, vt, n, opt, num_sms(), &P);
+  ss_status s = make_plan(op, kt, vt, n, opt, num_sms(), &P, num_inst);
   if (s != SS_OK) return s;
   if (ws_bytes < P.total) return SS_ERR_WORKSPACE_TOO_SMALL;
   const size_t kb = n * P.kbytes, vb = n * (vt == SS_U32 ? 4 : 8);
@@ -280,7 +302,8 @@ ss_status semisort_common(int op, ss_type kt, ss_type vt, const void* keys, cons
   w.out_k = keys_out;
   w.out_v = vals_out;
   w.has_vals = vals != nullptr;
-  w.splitter_mode = (op == kOpLess && opt) ? (uint32_t)opt->splitter_mode : 0u;
+  w.splitter_mode = (op == kOpLess && opt && num_inst == 0) ? (uint32_t)opt->splitter_mode : 0u;
+  w.offsets = d_offsets;
   cudaStream_t st = reinterpret_cast<cudaStream_t>(stream);
   PhaseTimer* tm = timer_for(opt, st);
   cudaError_t e = dispatch(op, kt, vals ? (int)vt : 2, P, w, st, tm);
@@ -291,8 +314,11 @@ ss_status semisort_common(int op, ss_type kt, ss_type vt, const void* keys, cons
 // collect-reduce (vals != NULL) and histogram (vals == NULL, counts in sums).
 ss_status reduce_common(int op, ss_type kt, const void* keys, const uint64_t* vals, void* ukeys, void* sums,
                         uint64_t capacity, uint64_t* d_num_unique, uint64_t n, void* ws, size_t ws_bytes,
-                        const ss_options* opt, ss_stream_t stream) {
+                        const ss_options* opt, ss_stream_t stream, const uint64_t* d_offsets = nullptr,
+                        uint32_t num_inst = 0, uint64_t* d_out_offsets = nullptr) {
   if (!d_num_unique || (reinterpret_cast<uintptr_t>(d_num_unique) & 7)) return SS_ERR_INVALID_ARG;
+  if (num_inst > 0 && (!d_offsets || !d_out_offsets || (reinterpret_cast<uintptr_t>(d_out_offsets) & 7)))
+    return SS_ERR_INVALID_ARG;
   cudaStream_t st = reinterpret_cast<cudaStream_t>(stream);
   const int kb1 = kbytes_of(kt);
   if (!kb1) return SS_ERR_INVALID_ARG;
@@ -300,14 +326,17 @@ ss_status reduce_common(int op, ss_type kt, const void* keys, const uint64_t* va
     if (ws && aligned16(ws) && ws_bytes >= sizeof(Ctrl)) {
       if (cudaMemsetAsync(ws, 0, sizeof(Ctrl), st) != cudaSuccess) return SS_ERR_CUDA;
     }
-    return cudaMemsetAsync(d_num_unique, 0, 8, st) == cudaSuccess ? SS_OK : SS_ERR_CUDA;
+    const size_t cnt = num_inst > 0 ? num_inst : 1;
+    if (cudaMemsetAsync(d_num_unique, 0, 8 * cnt, st) != cudaSuccess) return SS_ERR_CUDA;
+    if (num_inst > 0 && cudaMemsetAsync(d_out_offsets, 0, 8 * (cnt + 1), st) != cudaSuccess) return SS_ERR_CUDA;
+    return SS_OK;
   }
   if (!keys || !ukeys || !sums || !ws) return SS_ERR_INVALID_ARG;
   if (op == kOpReduce && !vals) return SS_ERR_INVALID_ARG;
   if (!aligned16(keys) || !aligned16(ukeys) || !aligned16(sums) || !aligned16(ws) || (vals && !aligned16(vals)))
     return SS_ERR_INVALID_ARG;
   Plan P;
-  ss_status s = make_plan(op, kt, SS_U64, n, opt, num_sms(), &P);
+  ss_status s = make_plan(op, kt, SS_U64, n, opt, num_sms(), &P, num_inst);
   if (s != SS_OK) return s;
   if (ws_bytes < P.total) return SS_ERR_WORKSPACE_TOO_SMALL;
   const uint64_t sb = op == kOpReduce ? 8 : 4;
@@ -316,7 +345,7 @@ ss_status reduce_common(int op, ss_type kt, const void* keys, const uint64_t* va
   Range ru{(uintptr_t)ukeys, (uintptr_t)ukeys + capacity * kb1};
   Range rs{(uintptr_t)sums, (uintptr_t)sums + capacity * sb};
   Range rw{(uintptr_t)ws, (uintptr_t)ws + P.total};
-  Range rn{(uintptr_t)d_num_unique, (uintptr_t)d_num_unique + 8};
+  Range rn{(uintptr_t)d_num_unique, (uintptr_t)d_num_unique + 8 * (num_inst > 0 ? num_inst : 1)};
   const Range outs[3] = {ru, rs, rn};
   for (const Range& o : outs) {
     if (overlap(o, rk) || overlap(o, rw) || (vals && overlap(o, rv))) return SS_ERR_INVALID_ARG;
@@ -335,6 +364,8 @@ ss_status reduce_common(int op, ss_type kt, const void* keys, const uint64_t* va
   w.sums_out = sums;
   w.num_unique = d_num_unique;
   w.out_capacity = capacity;
+  w.offsets = d_offsets;
+  w.inst_off_out = d_out_offsets;
   PhaseTimer* tm = timer_for(opt, st);
   cudaError_t e = dispatch(op, kt, op == kOpReduce ? (int)SS_U64 : 2, P, w, st, tm);
   if (e == cudaErrorNotSupported) return SS_ERR_UNSUPPORTED;
@@ -388,6 +419,51 @@ ss_status histogram(ss_type key_type, const void* keys, void* ukeys_out, uint32_
                     ss_stream_t stream) {
   return reduce_common(kOpHist, key_type, keys, nullptr, ukeys_out, counts_out, capacity, d_num_unique, n, ws,
                        ws_bytes, opt, stream);
+}
+
+ss_status ss_workspace_size_batched(int op, ss_type key_type, ss_type val_type, uint64_t n, uint32_t num_instances,
+                                    const ss_options* opt, size_t* bytes) {
+  if (!bytes || op < 0 || op > 3 || num_instances == 0) return SS_ERR_INVALID_ARG;
+  Plan P;
+  ss_status s = make_plan(op, key_type, val_type, n, opt, num_sms(), &P, num_instances);
+  if (s != SS_OK) return s;
+  *bytes = P.total;
+  return SS_OK;
+}
+
+ss_status semisort_equal_batched(ss_type key_type, ss_type val_type, const void* keys, const void* vals,
+                                 void* keys_out, void* vals_out, const uint64_t* d_offsets, uint32_t num_instances,
+                                 uint64_t n, void* ws, size_t ws_bytes, const ss_options* opt, ss_stream_t stream) {
+  if (num_instances == 0) return SS_ERR_INVALID_ARG;
+  return semisort_common(kOpEqual, key_type, val_type, keys, vals, keys_out, vals_out, n, ws, ws_bytes, opt,
+                         stream, d_offsets, num_instances);
+}
+
+ss_status semisort_less_batched(ss_type key_type, ss_type val_type, const void* keys, const void* vals,
+                                void* keys_out, void* vals_out, const uint64_t* d_offsets, uint32_t num_instances,
+                                uint64_t n, void* ws, size_t ws_bytes, const ss_options* opt, ss_stream_t stream) {
+  if (num_instances == 0) return SS_ERR_INVALID_ARG;
+  return semisort_common(kOpLess, key_type, val_type, keys, vals, keys_out, vals_out, n, ws, ws_bytes, opt,
+                         stream, d_offsets, num_instances);
+}
+
+ss_status collect_reduce_batched(ss_type key_type, const void* keys, const uint64_t* vals,
+                                 const uint64_t* d_offsets, uint32_t num_instances, uint64_t n, void* ukeys_out,
+                                 uint64_t* sums_out, uint64_t capacity, uint64_t* d_num_unique,
+                                 uint64_t* d_out_offsets, void* ws, size_t ws_bytes, const ss_options* opt,
+                                 ss_stream_t stream) {
+  if (num_instances == 0 || (n && !vals)) return SS_ERR_INVALID_ARG;
+  return reduce_common(kOpReduce, key_type, keys, vals, ukeys_out, sums_out, capacity, d_num_unique, n, ws,
+                       ws_bytes, opt, stream, d_offsets, num_instances, d_out_offsets);
+}
+
+ss_status histogram_batched(ss_type key_type, const void* keys, const uint64_t* d_offsets, uint32_t num_instances,
+                            uint64_t n, void* ukeys_out, uint32_t* counts_out, uint64_t capacity,
+                            uint64_t* d_num_unique, uint64_t* d_out_offsets, void* ws, size_t ws_bytes,
+                            const ss_options* opt, ss_stream_t stream) {
+  if (num_instances == 0) return SS_ERR_INVALID_ARG;
+  return reduce_common(kOpHist, key_type, keys, nullptr, ukeys_out, counts_out, capacity, d_num_unique, n, ws,
+                       ws_bytes, opt, stream, d_offsets, num_instances, d_out_offsets);
 }
 
 ss_status ss_last_device_error(void* ws, ss_stream_t stream, int* code) {

@@ -139,33 +139,90 @@ __device__ __forceinline__ uint32_t bucket_in(const K& k, const Seg& sg, const K
 // ----------------------------------------------------------------------------
 // init: reset the control block and seed level 0 (or a single base case).
 // ----------------------------------------------------------------------------
-static __global__ void k_init(Work w) {
-  if (threadIdx.x != 0) return;
+static __global__ void __launch_bounds__(1024) k_init(Work w) {
+  __shared__ uint32_t tmp[33];
+  __shared__ uint32_t carry[2];
+  __shared__ uint32_t bad;
   Ctrl* c = w.ctrl;
-  for (int l = 0; l < kMaxLevels; ++l) {
-    c->nsegs[l] = 0;
-    c->ntiles[l] = 0;
+  if (threadIdx.x == 0) {
+    for (int l = 0; l < kMaxLevels; ++l) {
+      c->nsegs[l] = 0;
+      c->ntiles[l] = 0;
+    }
+    c->nfin = 0;
+    c->error = 0;
+    for (int i = 0; i < 16; ++i) c->stats[i] = 0;
+    bad = 0;
+    carry[0] = carry[1] = 0;
   }
-  c->nfin = 0;
-  c->error = 0;
-  for (int i = 0; i < 16; ++i) c->stats[i] = 0;
+  __syncthreads();
   if (w.n == 0) return;
-  if (w.n <= w.alpha) {
-    Item it;
-    it.start = 0;
-    it.len = (uint32_t)w.n;
-    it.kind = kItemRefine;
-    it.buf = kBufIn;
-    it.aux = it.aux2 = 0;
-    it.level = 0;
-    w.items[0] = it;
-    c->nfin = 1;
-  } else {
-    Seg s = {};
-    s.start = 0;
-    s.len = (uint32_t)w.n;
-    w.segs[0][0] = s;
-    c->nsegs[0] = 1;
+  if (w.offsets == nullptr) {
+    if (threadIdx.x != 0) return;
+    if (w.n <= w.alpha) {
+      Item it;
+      it.start = 0;
+      it.len = (uint32_t)w.n;
+      it.kind = kItemRefine;
+      it.buf = kBufIn;
+      it.aux = it.aux2 = 0;
+      it.level = 0;
+      w.items[0] = it;
+      c->nfin = 1;
+    } else {
+      Seg s = {};
+      s.start = 0;
+      s.len = (uint32_t)w.n;
+      w.segs[0][0] = s;
+      c->nsegs[0] = 1;
+    }
+    return;
+  }
+  // batched: check the offsets, then instances of at most alpha records become
+  // base-case items and larger ones level-0 segments, both in instance order
+  const uint64_t* off = w.offsets;
+  const uint32_t ni = w.num_inst;
+  for (uint32_t i = threadIdx.x; i < ni; i += blockDim.x)
+    if (off[i] > off[i + 1]) bad = 1;
+  if (threadIdx.x == 0 && (off[0] != 0 || off[ni] != w.n)) bad = 1;
+  __syncthreads();
+  if (bad) {
+    if (threadIdx.x == 0) set_error(c, 1 /*SS_ERR_INVALID_ARG*/);
+    return;
+  }
+  for (uint32_t i0 = 0; i0 < ni; i0 += blockDim.x) {
+    const uint32_t i = i0 + threadIdx.x;
+    const uint64_t len = i < ni ? off[i + 1] - off[i] : 0;
+    const uint32_t small = len > 0 && len <= w.alpha, big = len > w.alpha;
+    uint32_t ts, tb;
+    const uint32_t es = block_exclusive_scan(small, tmp, &ts);
+    const uint32_t eb = block_exclusive_scan(big, tmp, &tb);
+    if (small) {
+      Item it;
+      it.start = off[i];
+      it.len = (uint32_t)len;
+      it.kind = kItemRefine;
+      it.buf = kBufIn;
+      it.aux = it.aux2 = 0;
+      it.level = kDirectLevel;
+      w.items[carry[0] + es] = it;
+    }
+    if (big) {
+      Seg s = {};
+      s.start = off[i];
+      s.len = (uint32_t)len;
+      w.segs[0][carry[1] + eb] = s;
+    }
+    __syncthreads();
+    if (threadIdx.x == 0) {
+      carry[0] += ts;
+      carry[1] += tb;
+    }
+    __syncthreads();
+  }
+  if (threadIdx.x == 0) {
+    c->nfin = carry[0];
+    c->nsegs[0] = carry[1];
   }
 }
 
@@ -191,14 +248,15 @@ __global__ void __launch_bounds__(1024) k_plan(Work w, int level) {
     if (s < ns) {
       sg = segs[s];
       uint32_t lb;
-      if (level == 0) {
+      const bool top_single = level == 0 && w.num_inst <= 1;
+      if (top_single) {
         lb = w.lbits1;
       } else {
         const uint64_t want = (2ull * sg.len + w.alpha - 1) / w.alpha;
         lb = want <= 2 ? 1u : (uint32_t)(64 - __clzll(want - 1));
         lb = lb > (uint32_t)kMaxLightLog2 ? (uint32_t)kMaxLightLog2 : lb;
       }
-      if (OP == kOpLess && level > 0 && lb > kMaxLightLog2 - 1) lb = kMaxLightLog2 - 1;
+      if (OP == kOpLess && !top_single && lb > kMaxLightLog2 - 1) lb = kMaxLightLog2 - 1;
       const uint32_t nl = 1u << lb;
       sg.lbits = lb;
       // semisort_<: q <= (n_L - 1) + n_L boundaries give 2q + 1 < 4 n_L bucket ids
@@ -270,7 +328,7 @@ __global__ void __launch_bounds__(1024) k_sample(Work w, LevelBufs lb, uint32_t 
   __shared__ uint32_t tab[4 * kMaxHeavy];
   __shared__ uint32_t tmp[33];
   __shared__ uint32_t nh_sh;
-  if (TopWide<K, OP>::value && lb.level == 0) return;  // the wide top level uses k_less_split
+  if (TopWide<K, OP>::value && lb.level == 0 && w.num_inst <= 1) return;  // the wide top level uses k_less_split
   const uint32_t ns = w.ctrl->nsegs[lb.level];
   for (uint32_t s = blockIdx.x; s < ns; s += gridDim.x) {
     const Seg sg = w.segs[lb.level][s];
@@ -1080,7 +1138,7 @@ __global__ void __launch_bounds__(1024) k_emit(Work w, LevelBufs lb) {
         if (heavy && (OP == kOpReduce || OP == kOpHist)) {
           if (i0 < w.item_cap) {
             Item it;
-            it.start = 0;
+            it.start = sg.start;  // (locates the instance of a batched call)
             it.len = sz;
             it.kind = kItemHeavyOut;
             it.buf = 0;
@@ -1579,7 +1637,7 @@ static __global__ void __launch_bounds__(1024) k_iscan_b(Work w) {
     if (threadIdx.x == 0) carry += tot;
     __syncthreads();
   }
-  if (threadIdx.x == 0) {
+  if (threadIdx.x == 0 && w.offsets == nullptr) {
     *w.num_unique = carry;
     if (carry > w.out_capacity) set_error(w.ctrl, 4 /*SS_ERR_CAPACITY*/);
   }
@@ -1607,6 +1665,83 @@ static __global__ void __launch_bounds__(1024) k_iscan_c(Work w) {
   }
 }
 
+// Batched collect-reduce / histogram output placement.  Within each item
+// class (base-case items of small instances, then the items of distribution
+// levels 0..3, in the order the list holds them) the items are grouped by
+// instance in instance order, so an instance's outputs in one class occupy one
+// range of the item scan.  Per (class, instance): the outputs and the first
+// scan position (order-independent atomics, so deterministic); then one scan
+// over instances gives every instance its output offset and every (class,
+// instance) its base: instance offset + outputs of earlier classes.
+__device__ __forceinline__ uint32_t item_class(const Item& it) {
+  return it.level == kDirectLevel ? 0u : it.level + 1u;
+}
+__device__ __forceinline__ uint32_t instance_of(const Work& w, uint64_t start) {
+  uint32_t lo = 0, hi = w.num_inst;  // last instance whose first record <= start
+  while (hi - lo > 1) {
+    const uint32_t mid = (lo + hi) >> 1;
+    if (w.offsets[mid] <= start)
+      lo = mid;
+    else
+      hi = mid;
+  }
+  return lo;
+}
+
+static __global__ void k_inst_reset(Work w) {
+  const uint32_t m = 5 * w.num_inst;
+  for (uint32_t i = blockIdx.x * blockDim.x + threadIdx.x; i < m; i += gridDim.x * blockDim.x) {
+    w.inst_base[i] = 0;
+    w.inst_first[i] = ~0ull;
+  }
+}
+
+static __global__ void k_inst_accum(Work w) {
+  const uint32_t nfin = w.ctrl->nfin;
+  for (uint32_t i = blockIdx.x * blockDim.x + threadIdx.x; i < nfin; i += gridDim.x * blockDim.x) {
+    const Item it = w.items[i];
+    const uint32_t k = item_class(it) * w.num_inst + instance_of(w, it.start);
+    atomicAdd((unsigned long long*)&w.inst_base[k], (unsigned long long)w.item_out[i]);
+    atomicMin((unsigned long long*)&w.inst_first[k], (unsigned long long)w.item_pos[i]);
+  }
+}
+
+static __global__ void __launch_bounds__(1024) k_inst_scan(Work w) {
+  __shared__ uint64_t tmp[33];
+  __shared__ uint64_t carry;
+  const uint32_t ni = w.num_inst;
+  if (threadIdx.x == 0) carry = 0;
+  __syncthreads();
+  for (uint32_t i0 = 0; i0 < ni; i0 += blockDim.x) {
+    const uint32_t i = i0 + threadIdx.x;
+    uint64_t u[5], tot = 0;
+#pragma unroll
+    for (int c = 0; c < 5; ++c) {
+      u[c] = i < ni ? w.inst_base[(uint64_t)c * ni + i] : 0;
+      tot += u[c];
+    }
+    uint64_t all;
+    const uint64_t ex = carry + block_exclusive_scan64(tot, tmp, &all);
+    if (i < ni) {
+      w.num_unique[i] = tot;
+      w.inst_off_out[i] = ex;
+      uint64_t b = ex;
+#pragma unroll
+      for (int c = 0; c < 5; ++c) {
+        w.inst_base[(uint64_t)c * ni + i] = b;
+        b += u[c];
+      }
+    }
+    __syncthreads();
+    if (threadIdx.x == 0) carry += all;
+    __syncthreads();
+  }
+  if (threadIdx.x == 0) {
+    w.inst_off_out[ni] = carry;
+    if (carry > w.out_capacity) set_error(w.ctrl, 4 /*SS_ERR_CAPACITY*/);
+  }
+}
+
 // One warp per item.  Outputs at positions >= capacity are not written.
 template <class K, class V, int OP>
 __global__ void __launch_bounds__(256) k_pack(Work w) {
@@ -1618,7 +1753,11 @@ __global__ void __launch_bounds__(256) k_pack(Work w) {
   const uint64_t cap = w.out_capacity;
   for (uint32_t itx = gw; itx < nfin; itx += nwarps) {
     const Item it = w.items[itx];
-    const uint64_t pos = w.item_pos[itx];
+    uint64_t pos = w.item_pos[itx];
+    if (w.offsets) {
+      const uint32_t k = item_class(it) * w.num_inst + instance_of(w, it.start);
+      pos = w.inst_base[k] + (pos - w.inst_first[k]);
+    }
     if (it.kind == kItemHeavyOut) {
       if (lane == 0 && pos < cap) {
         const Seg sg = w.segs[it.level][it.aux];

@@ -3,14 +3,32 @@
 #pragma once
 #include <cuda_runtime.h>
 
+#include <mutex>
+#include <utility>
+#include <vector>
+
 #include "ss_host.h"
 #include "ss_kernels.cuh"
 
 namespace ss {
 
+// Raise a kernel's dynamic shared-memory limit once per (kernel, device); the
+// attribute persists, so later calls -- including ones being captured into a
+// CUDA graph -- make no runtime call for it.
 template <class F>
 static cudaError_t set_smem(F* f, size_t bytes) {
-  return cudaFuncSetAttribute(f, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes);
+  static std::mutex mu;
+  static std::vector<std::pair<const void*, int>> done;
+  int dev = 0;
+  cudaError_t e = cudaGetDevice(&dev);
+  if (e != cudaSuccess) return e;
+  const void* key = reinterpret_cast<const void*>(f);
+  std::lock_guard<std::mutex> g(mu);
+  for (const auto& d : done)
+    if (d.first == key && d.second == dev) return cudaSuccess;
+  e = cudaFuncSetAttribute(f, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes);
+  if (e == cudaSuccess) done.emplace_back(key, dev);
+  return e;
 }
 
 // Buffer roles.  Level 0 reads the caller's input (structure of arrays) and
@@ -84,7 +102,7 @@ cudaError_t launch_pipeline(const Plan& P, const Work& w, cudaStream_t st, const
   if ((e = set_smem(k_sample<K, V, OP>, (size_t)s_cap_max * sizeof(K))) != cudaSuccess) return e;
 
   int& nl = *cfg.launches;
-  k_init<<<1, 32, 0, st>>>(w);
+  k_init<<<1, 1024, 0, st>>>(w);
   ++nl;
   if (tm) tm->mark("init");
   if (P.n > P.alpha) {
@@ -93,7 +111,7 @@ cudaError_t launch_pipeline(const Plan& P, const Work& w, cudaStream_t st, const
       const uint32_t segs = P.seg_cap[level];
       const uint32_t tiles = P.tile_cap[level];
       auto cap = [](uint32_t want, uint32_t lim) { return want < lim ? (want ? want : 1) : lim; };
-      const bool top_wide = kWide && level == 0;
+      const bool top_wide = kWide && level == 0 && w.num_inst <= 1;
       k_plan<OP><<<1, 1024, 0, st>>>(w, level);
       if (tm) tm->mark(level == 0 ? "plan.L0" : "plan.L1+");
       if (top_wide) {
@@ -154,6 +172,13 @@ cudaError_t launch_pipeline(const Plan& P, const Work& w, cudaStream_t st, const
     k_iscan_a<<<nch, 1024, 0, st>>>(w);
     k_iscan_b<<<1, 1024, 0, st>>>(w);
     k_iscan_c<<<nch, 1024, 0, st>>>(w);
+    if (w.offsets) {  // batched: make each instance's outputs contiguous
+      const uint32_t g = (5 * w.num_inst + 255) / 256;
+      k_inst_reset<<<g < 1024 ? g : 1024, 256, 0, st>>>(w);
+      k_inst_accum<<<nsm * 4, 256, 0, st>>>(w);
+      k_inst_scan<<<1, 1024, 0, st>>>(w);
+      nl += 3;
+    }
     if (tm) tm->mark("scan_out");
     k_pack<K, V, OP><<<nsm * 8, 256, 0, st>>>(w);
     if (tm) tm->mark("pack");

@@ -30,6 +30,10 @@ enum Op : int { kOpEqual = 0, kOpLess = 1, kOpReduce = 2, kOpHist = 3 };
 // Buffer ids used by work items.
 enum Buf : uint32_t { kBufIn = 0, kBufT = 1, kBufOut = 2, kBufT2 = 3 };
 
+// Finish items of a batched call's instances of at most alpha records carry
+// this level tag (they go straight to the base case).
+constexpr uint32_t kDirectLevel = kMaxLevels;
+
 // Finish-item kinds.
 enum ItemKind : uint32_t { kItemRefine = 0, kItemCopy = 1, kItemHeavyOut = 2 };
 
@@ -125,6 +129,12 @@ struct Work {
   void* bigs_tmp;       // its sorted runs before the merge
   void* learn;          // semisort_<: learned-splitter state (LearnState)
   uint32_t splitter_mode;  // 0 sampled, 1 learned (semisort_< top level)
+  // batched calls: instance i holds records [offsets[i], offsets[i+1])
+  const uint64_t* offsets;  // device, num_inst + 1 entries; null for a single instance
+  uint32_t num_inst;
+  uint64_t* inst_base;      // collect-reduce / histogram: per (class, instance) output base (5 x num_inst)
+  uint64_t* inst_first;     // per (class, instance) first item position in the item scan
+  uint64_t* inst_off_out;   // user: num_inst + 1 output offsets
   uint32_t* scratch32;  // histogram: per-position counts of compacted base cases
   uint64_t* item_aux;   // collect-reduce: heavy totals per item
   uint64_t out_capacity;
@@ -144,7 +154,8 @@ struct Plan {
       off_htab[kMaxLevels], off_bsize[kMaxLevels], off_boff[kMaxLevels], off_hpart[kMaxLevels],
       off_split[kMaxLevels];
   size_t off_items, off_item_out, off_item_pos, off_block_sums, off_ctrl, off_scratch32, off_item_aux;
-  size_t off_bigs, off_bigs_tmp, off_learn;
+  size_t off_bigs, off_bigs_tmp, off_learn, off_inst_base, off_inst_first;
+  uint32_t num_inst;
   size_t total;
 };
 
