@@ -239,6 +239,114 @@ def time_op(ss, sg, torch, name, keys, dists, vals, kout, vout, ws, n, stream):
     return out
 
 
+BATCH_SEED = 0x5EED0004
+
+
+def batched_workload(sg, torch, ni=4096, lo=8, hi=22):
+    """4096 instances of floor(2^U[8,22]) records; instance i draws Zipf keys
+    with s ~ U[0.6, 1.5] over D ~ floor(exp(U[ln 10, ln size])) ranks, ranks
+    hashed with the instance's own seed (keys differ across instances)."""
+    import numpy as np
+
+    import synth
+    idx = np.arange(ni, dtype=np.uint64)
+    sizes = np.floor(2.0 ** (lo + (hi - lo) * synth.unit(synth.rand64(BATCH_SEED, 0x1A, idx)))).astype(np.int64)
+    s_i = 0.6 + 0.9 * synth.unit(synth.rand64(BATCH_SEED, 0x1B, idx))
+    ud = synth.unit(synth.rand64(BATCH_SEED, 0x1C, idx))
+    d_i = np.maximum(2, np.floor(np.exp(np.log(10) + (np.log(np.maximum(sizes, 10)) - np.log(10)) * ud)))
+    off = np.concatenate([[0], np.cumsum(sizes)]).astype(np.int64)
+    n = int(off[-1])
+    keys = torch.empty(n, dtype=torch.uint64, device="cuda")
+    for i in range(ni):
+        if sizes[i]:
+            sg.zipf(BATCH_SEED + 1 + i, int(sizes[i]), float(s_i[i]), N=int(d_i[i]), out=keys[off[i]:off[i + 1]])
+    return off, keys, n
+
+
+def bench_batched(ss, sg, torch, stream, reps=3):
+    """The batched forms on the 4096-instance workload: one autotuned call
+    (eager, and captured once in a CUDA graph and replayed) against one plain
+    call per instance, for semisort_= and collect-reduce."""
+    import numpy as np
+
+    from paper_2304_10078_gb300.autotune import CANDIDATES, Tuner
+    off_h, keys, n = batched_workload(sg, torch)
+    ni = len(off_h) - 1
+    off = torch.from_numpy(off_h).cuda().view(torch.uint64)
+    vals = sg.iota(n)
+    kout, vout = torch.empty_like(keys), torch.empty_like(vals)
+    nu = torch.zeros(ni, dtype=torch.uint64, device="cuda")
+    oo = torch.zeros(ni + 1, dtype=torch.uint64, device="cuda")
+    tuner = Tuner()
+    big = int(np.max(np.diff(off_h)))
+    res = {"workload": f"{ni} instances, {n} records (u64 key, u64 value = index), sizes floor(2^U[8,22]), "
+                       "per-instance Zipf s ~ U[0.6,1.5] over floor(exp(U[ln 10, ln size])) ranks"}
+
+    def timed(fn, k):
+        a = torch.cuda.Event(enable_timing=True)
+        b = torch.cuda.Event(enable_timing=True)
+        a.record(stream)
+        for _ in range(k):
+            fn()
+        b.record(stream)
+        b.synchronize()
+        return a.elapsed_time(b) / k
+
+    for op in ("semisort_equal", "collect_reduce"):
+        code = ss.OP_EQUAL if op == "semisort_equal" else ss.OP_REDUCE
+        ws_bytes = max(ss.workspace_size_batched(code, ss.SS_U64, ss.SS_U64, n, ni, ss.make_options(**c))
+                       for c in CANDIDATES + [{}])
+        ws = torch.empty(ws_bytes, dtype=torch.uint8, device="cuda")
+
+        def run(opt, st=None):
+            if op == "semisort_equal":
+                ss.semisort_equal_batched(keys, vals, off, keys_out=kout, vals_out=vout, workspace=ws, options=opt,
+                                          stream=st)
+            else:
+                ss.collect_reduce_batched(keys, vals, off, capacity=n, ukeys_out=kout, sums_out=vout, num_unique=nu,
+                                          out_offsets=oo, workspace=ws, options=opt, stream=st)
+
+        opt, tune_ms = tuner.best(op + "_batched", n, ni, run)
+        eager_ms = timed(lambda: run(opt), reps)
+        launches = ss.kernel_launches()
+        assert ss.last_device_error(ws) == 0
+        side = torch.cuda.Stream()
+        side.wait_stream(torch.cuda.current_stream())
+        g = torch.cuda.CUDAGraph()
+        with torch.cuda.graph(g, stream=side):
+            run(opt, side)
+        torch.cuda.synchronize()
+        graph_ms = timed(g.replay, reps)
+        assert ss.last_device_error(ws) == 0
+        del g
+        # one plain call per instance (untuned defaults), on the same stream
+        plain = ss.make_options(seed=1)
+        ws1 = ss.alloc_workspace(code, keys[:big], vals[:big], plain)
+        nu1 = torch.zeros(1, dtype=torch.uint64, device="cuda")
+
+        def per_instance():
+            for i in range(ni):
+                a, b = int(off_h[i]), int(off_h[i + 1])
+                if a == b:
+                    continue
+                if op == "semisort_equal":
+                    ss.semisort_equal(keys[a:b], vals[a:b], keys_out=kout[a:b], vals_out=vout[a:b], workspace=ws1,
+                                      options=plain)
+                else:
+                    ss.collect_reduce(keys[a:b], vals[a:b], capacity=b - a, ukeys_out=kout[a:b], sums_out=vout[a:b],
+                                      num_unique=nu1, workspace=ws1, options=plain)
+        per_ms = timed(per_instance, 1)
+        assert ss.last_device_error(ws1) == 0
+        del ws, ws1
+        res[op] = {"unit": UNIT, "batched_graph": n / (graph_ms / 1000) / 1e9,
+                   "batched_eager": n / (eager_ms / 1000) / 1e9, "per_instance_calls": n / (per_ms / 1000) / 1e9,
+                   "ms": {"batched_graph": graph_ms, "batched_eager": eager_ms, "per_instance_calls": per_ms},
+                   "kernel_launches_per_batched_call": launches,
+                   "tuned_options": {k: getattr(opt, k) for k in ("subarray", "alpha", "n_light_log2")},
+                   "tuning_ms": tune_ms}
+    return res
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -251,7 +359,7 @@ def main():
     ap.add_argument("--e2e-steps", type=int, default=3)
     ap.add_argument("--quick", action="store_true", help="small smoke configuration (not a bench number)")
     ap.add_argument("--dists", default="", help="comma-separated indices into the distribution list")
-    ap.add_argument("--ops", default="collect_reduce,histogram,semisort_less,semisort_less_learned",
+    ap.add_argument("--ops", default="collect_reduce,histogram,semisort_less,semisort_less_learned,batched",
                     help="further operations timed after the headline (empty: none)")
     args = ap.parse_args()
 
@@ -286,7 +394,8 @@ def main():
     ops = [o for o in args.ops.split(",") if o]
     op_codes = {"semisort_equal": ss.OP_EQUAL, "collect_reduce": ss.OP_REDUCE, "histogram": ss.OP_HIST,
                 "semisort_less": ss.OP_LESS, "semisort_less_learned": ss.OP_LESS}
-    ws_bytes = max(ss.workspace_size(op_codes[o], ss.SS_U64, ss.SS_U64, n, opt) for o in ["semisort_equal"] + ops)
+    ws_bytes = max(ss.workspace_size(op_codes[o], ss.SS_U64, ss.SS_U64, n, opt)
+                   for o in ["semisort_equal"] + ops if o in op_codes)
     ws = torch.empty(ws_bytes, dtype=torch.uint8, device="cuda")
     stream = torch.cuda.current_stream()
 
@@ -378,7 +487,13 @@ def main():
 
     by_op = {}
     for o in ops:
-        by_op[o] = time_op(ss, sg, torch, o, keys, dists, vals, kout, vout, ws, n, stream)
+        if o != "batched":
+            by_op[o] = time_op(ss, sg, torch, o, keys, dists, vals, kout, vout, ws, n, stream)
+    if "batched" in ops:
+        keys.clear()
+        del ws, kout, vout, vals
+        torch.cuda.empty_cache()
+        by_op["batched"] = bench_batched(ss, sg, torch, stream, reps=3)
 
     if rank != 0:
         if world > 1:

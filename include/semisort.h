@@ -12,7 +12,9 @@
  *    keys[n] and vals[n].  Key types: SS_U32, SS_U64, SS_U128 (16 bytes,
  *    little-endian lo then hi, ordered as an unsigned 128-bit integer).  Value
  *    types: SS_U32, SS_U64.
- *  - All pointers are DEVICE pointers owned by the caller, 16-byte aligned.
+ *  - All pointers are DEVICE pointers owned by the caller.  Key, value and
+ *    output arrays need the alignment of their element type (4, 8 or 16
+ *    bytes); the workspace must be 16-byte aligned.
  *    The library never allocates device memory: scratch space comes from the
  *    caller's workspace `ws` of `ws_bytes` bytes, sized by
  *    ss_workspace_size() for the same (op, types, n, options).

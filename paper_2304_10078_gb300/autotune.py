@@ -1,0 +1,70 @@
+"""Autotuner for the batched forms: picks the subarray size l, the base-case
+threshold alpha and the top-level light-bucket count n_L for a size class by
+timing candidate settings on the caller's own input (CUDA events on the
+launching stream, one warm-up call per candidate).  Choices are cached per
+(GPU name, operation, size class), in memory and optionally in a JSON file.
+
+Only the speed depends on these settings; every candidate gives the same
+result class (exact semisort / reduce), so tuning never changes correctness.
+"""
+from __future__ import annotations
+
+import json
+import math
+import os
+
+CANDIDATES = [
+    {"subarray": 1 << 16, "alpha": 4096},
+    {"subarray": 1 << 18, "alpha": 4096},
+    {"subarray": 1 << 20, "alpha": 4096},
+    {"subarray": 1 << 18, "alpha": 2048},
+    {"subarray": 1 << 18, "alpha": 4096, "n_light_log2": 8},
+]
+
+
+def size_class(n: int, num_instances: int) -> str:
+    """Instances and mean instance size, each rounded to a power of two."""
+    mean = max(1, n // max(1, num_instances))
+    return f"i2^{round(math.log2(max(1, num_instances)))}-m2^{round(math.log2(mean))}"
+
+
+class Tuner:
+    def __init__(self, cache_path: str | None = None):
+        self.cache_path = cache_path
+        self.cache: dict = {}
+        if cache_path and os.path.exists(cache_path):
+            with open(cache_path) as f:
+                self.cache = json.load(f)
+
+    def _key(self, op: str, n: int, num_instances: int) -> str:
+        import torch
+        return f"{torch.cuda.get_device_name()}|{op}|{size_class(n, num_instances)}"
+
+    def best(self, op: str, n: int, num_instances: int, run, seed: int = 1, candidates=None):
+        """Options for `run(options)` (which enqueues one call on the current
+        stream): the cached choice for this size class, or the fastest of the
+        candidates.  Returns (options, {candidate: ms})."""
+        import torch
+
+        import paper_2304_10078_gb300 as ss
+        key = self._key(op, n, num_instances)
+        if key in self.cache:
+            return ss.make_options(seed=seed, **self.cache[key]["choice"]), self.cache[key]["ms"]
+        stream = torch.cuda.current_stream()
+        timings = {}
+        for cand in candidates or CANDIDATES:
+            opt = ss.make_options(seed=seed, **cand)
+            run(opt)
+            a = torch.cuda.Event(enable_timing=True)
+            b = torch.cuda.Event(enable_timing=True)
+            a.record(stream)
+            run(opt)
+            b.record(stream)
+            b.synchronize()
+            timings[json.dumps(cand, sort_keys=True)] = a.elapsed_time(b)
+        choice = json.loads(min(timings, key=timings.get))
+        self.cache[key] = {"choice": choice, "ms": timings}
+        if self.cache_path:
+            with open(self.cache_path, "w") as f:
+                json.dump(self.cache, f, indent=1)
+        return ss.make_options(seed=seed, **choice), timings

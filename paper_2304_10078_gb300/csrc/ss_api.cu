@@ -229,6 +229,8 @@ void fill_work(const Plan& P, void* ws, Work* w) {
 }
 
 bool aligned16(const void* p) { return (reinterpret_cast<uintptr_t>(p) & 15) == 0; }
+// Caller arrays are accessed element by element: each needs its element's alignment.
+bool aligned_to(const void* p, size_t bytes) { return (reinterpret_cast<uintptr_t>(p) & (bytes - 1)) == 0; }
 
 struct Range {
   uintptr_t a, b;
@@ -273,9 +275,13 @@ ss_status semisort_common(int op, ss_type kt, ss_type vt, const void* keys, cons
   if (n == 0) return SS_OK;
   if (!keys || !keys_out || !ws) return SS_ERR_INVALID_ARG;
   if ((vals == nullptr) != (vals_out == nullptr)) return SS_ERR_INVALID_ARG;
-  if (!aligned16(keys) || !aligned16(keys_out) || !aligned16(ws) || (vals && !aligned16(vals)) ||
-      (vals_out && !aligned16(vals_out)))
-    return SS_ERR_INVALID_ARG;
+  {
+    const size_t ka = (size_t)kbytes_of(kt), va = vt == SS_U32 ? 4 : 8;
+    if (!ka) return SS_ERR_INVALID_ARG;
+    if (!aligned_to(keys, ka) || !aligned_to(keys_out, ka) || !aligned16(ws) || (vals && !aligned_to(vals, va)) ||
+        (vals_out && !aligned_to(vals_out, va)) || (d_offsets && !aligned_to(d_offsets, 8)))
+      return SS_ERR_INVALID_ARG;
+  }
   Plan P;
   ss_status s = make_plan(op, kt, vt, n, opt, num_sms(), &P, num_inst);
   if (s != SS_OK) return s;
@@ -333,7 +339,8 @@ ss_status reduce_common(int op, ss_type kt, const void* keys, const uint64_t* va
   }
   if (!keys || !ukeys || !sums || !ws) return SS_ERR_INVALID_ARG;
   if (op == kOpReduce && !vals) return SS_ERR_INVALID_ARG;
-  if (!aligned16(keys) || !aligned16(ukeys) || !aligned16(sums) || !aligned16(ws) || (vals && !aligned16(vals)))
+  if (!aligned_to(keys, kb1) || !aligned_to(ukeys, kb1) || !aligned_to(sums, op == kOpReduce ? 8 : 4) ||
+      !aligned16(ws) || (vals && !aligned_to(vals, 8)) || (d_offsets && !aligned_to(d_offsets, 8)))
     return SS_ERR_INVALID_ARG;
   Plan P;
   ss_status s = make_plan(op, kt, SS_U64, n, opt, num_sms(), &P, num_inst);
@@ -593,7 +600,7 @@ namespace {
 ss_status mlp_setup(const float* d_params, const float* d_x, const float* d_t, uint32_t m, void* ws, size_t ws_bytes,
                     cudaStream_t st, LearnState** out) {
   if (!ws || !aligned16(ws) || ws_bytes < sizeof(LearnState)) return SS_ERR_WORKSPACE_TOO_SMALL;
-  if (m > (uint32_t)(kGradCTAsMax * kGradThreads)) return SS_ERR_UNSUPPORTED;
+  if (m > (uint32_t)(kGradCTAsMax * kGradPts)) return SS_ERR_UNSUPPORTED;
   LearnState* L = reinterpret_cast<LearnState*>(ws);
   if (d_params && cudaMemcpyAsync(L->p, d_params, sizeof(float) * kMlpParams, cudaMemcpyDeviceToDevice, st) != cudaSuccess)
     return SS_ERR_CUDA;
@@ -615,7 +622,7 @@ extern "C" ss_status ss_mlp_loss_grad(const float* d_params, const float* d_x, c
   ss_status s = mlp_setup(d_params, d_x, d_t, m, ws, ws_bytes, st, &L);
   if (s != SS_OK) return s;
   k_learn_range<<<1, 32, 0, st>>>(L, 0, 1, m);
-  k_learn_step<<<(m + kGradThreads - 1) / kGradThreads, kGradThreads, 0, st>>>(L, 0, 0.0f);
+  k_learn_step<<<(m + kGradPts - 1) / kGradPts, kGradThreads, 0, st>>>(L, 0, 0.0f);
   if (cudaMemcpyAsync(d_out, L->grad, sizeof(float) * (kMlpParams + 1), cudaMemcpyDeviceToDevice, st) != cudaSuccess)
     return SS_ERR_CUDA;
   return cudaGetLastError() == cudaSuccess ? SS_OK : SS_ERR_CUDA;
@@ -630,7 +637,7 @@ extern "C" ss_status ss_mlp_train(const float* d_x, const float* d_t, uint32_t m
   ss_status s = mlp_setup(d_params0, d_x, d_t, m, ws, ws_bytes, st, &L);
   if (s != SS_OK) return s;
   k_learn_range<<<1, 32, 0, st>>>(L, 0, 1, m);
-  const uint32_t ctas = (m + kGradThreads - 1) / kGradThreads;
+  const uint32_t ctas = (m + kGradPts - 1) / kGradPts;
   for (uint32_t i = 1; i <= steps; ++i) k_learn_step<<<ctas, kGradThreads, 0, st>>>(L, (int)i, lr);
   k_learn_step<<<ctas, kGradThreads, 0, st>>>(L, 0, 0.0f);  // loss at the final parameters
   if (cudaMemcpyAsync(d_params_out, L->p, sizeof(float) * kMlpParams, cudaMemcpyDeviceToDevice, st) != cudaSuccess)

@@ -125,7 +125,7 @@ cudaError_t launch_pipeline(const Plan& P, const Work& w, cudaStream_t st, const
           ls = reinterpret_cast<LearnState*>(w.learn);
           k_learn_prep<K><<<1, 1024, 0, st>>>(reinterpret_cast<const K*>(w.bigs), ls, w.seed);
           for (int s = 1; s <= kLearnSteps; ++s)
-            k_learn_step<<<kLearnPts / kGradThreads, kGradThreads, 0, st>>>(ls, s, kLearnLr);
+            k_learn_step<<<kLearnPts / kGradPts, kGradThreads, 0, st>>>(ls, s, kLearnLr);
           k_learn_invert<K><<<((1u << kLessTopLog2) + 255) / 256, 256, 0, st>>>(ls, w.segs[0], 0);
           nl += kLearnSteps + 2;
           if (tm) tm->mark("learn.L0");

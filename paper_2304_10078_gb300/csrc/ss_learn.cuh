@@ -23,8 +23,7 @@ constexpr int kH = 32;
 constexpr int kMlpParams = 4 * kH + kH * kH + 1;  // 1153
 constexpr int kOffV1 = 0, kOffC1 = kH, kOffV2 = 2 * kH, kOffC2 = 2 * kH + kH * kH, kOffV3 = 3 * kH + kH * kH,
               kOffC3 = 4 * kH + kH * kH;
-constexpr int kGradThreads = 64;   // points per CTA of a gradient step
-constexpr int kGradCTAsMax = 64;   // at most 4096 points
+constexpr int kGradCTAsMax = 64;   // at most 64 x 64 = 4096 points
 constexpr int kLearnPts = 1024;    // training points drawn from the sorted sample
 constexpr int kLearnSteps = 800;
 constexpr float kLearnLr = 0.01f;
@@ -35,8 +34,8 @@ struct LearnState {
   float v[kMlpParams];  // Adam second moment
   float partial[kGradCTAsMax][kMlpParams + 1];  // per-CTA gradient and squared-error sum
   float grad[kMlpParams + 1];                   // last summed gradient and loss
-  float x[kGradCTAsMax * kGradThreads];
-  float t[kGradCTAsMax * kGradThreads];
+  float x[kGradCTAsMax * 64];
+  float t[kGradCTAsMax * 64];
   uint64_t kmin, kmax;   // key range of the normalization
   uint32_t npts;
   uint32_t done;         // CTAs finished in the current step (reset by the last one)
@@ -87,19 +86,22 @@ __device__ __forceinline__ float mlp_eval(const MlpSmem& s, float x) {
 }
 
 // One full-batch gradient step over L->npts points.  Each CTA handles 64
-// points (one per thread) and writes its gradient sums; the last CTA to
-// finish adds the partial sums in CTA order (a fixed order, so the result is
-// deterministic) and, when step > 0, applies Adam step `step`.  No CTA waits
-// for another.
+// points with 256 threads: four threads per point, each owning 8 of the 32
+// units of a layer (h1, h2 and the backward terms go through shared memory).
+// The CTA writes its gradient sums; the last CTA to finish adds the partial
+// sums in CTA order (a fixed order, so the result is deterministic) and, when
+// step > 0, applies Adam step `step`.  No CTA waits for another.
+constexpr int kGradThreads = 256;  // threads per CTA of a gradient step
+constexpr int kGradPts = 64;       // points per CTA
 struct GradSmem {
   MlpSmem mw;
-  float h1[kGradThreads][kH + 1];
-  float h2[kGradThreads][kH + 1];
-  float d1[kGradThreads][kH + 1];
-  float d2[kGradThreads][kH + 1];
-  float e[kGradThreads];
-  float x[kGradThreads];
-  float se[kGradThreads];
+  float h1[kGradPts][kH + 1];
+  float h2[kGradPts][kH + 1];
+  float d1[kGradPts][kH + 1];
+  float d2[kGradPts][kH + 1];
+  float e[kGradPts];
+  float x[kGradPts];
+  float se[kGradPts];
   uint32_t last;
 };
 
@@ -108,44 +110,57 @@ static __global__ void __launch_bounds__(kGradThreads) k_learn_step(LearnState* 
   const int tid = threadIdx.x;
   const uint32_t npts = L->npts;
   mlp_load(gs.mw, L->p);
-  __syncthreads();
-  const uint32_t pt = blockIdx.x * kGradThreads + tid;
+  const int q = tid >> 2;         // point within the CTA
+  const int part = tid & 3;       // which 8 units this thread owns
+  const int u0 = part * 8;
+  const uint32_t pt = blockIdx.x * kGradPts + q;
   const bool live = pt < npts;
   const float x = live ? L->x[pt] : 0.0f;
   const float t = live ? L->t[pt] : 0.0f;
+  __syncthreads();
   // forward
+#pragma unroll
+  for (int i = 0; i < 8; ++i) gs.h1[q][u0 + i] = sigmf(fmaf(gs.mw.w1[u0 + i], x, gs.mw.c1[u0 + i]));
+  __syncthreads();
   float h1[kH];
 #pragma unroll
-  for (int i = 0; i < kH; ++i) h1[i] = sigmf(fmaf(gs.mw.w1[i], x, gs.mw.c1[i]));
-  float y = gs.mw.c3;
-  for (int j = 0; j < kH; ++j) {
+  for (int i = 0; i < kH; ++i) h1[i] = gs.h1[q][i];
+  float yp = 0.0f, h2v[8];
+#pragma unroll
+  for (int jj = 0; jj < 8; ++jj) {
+    const int j = u0 + jj;
     float z = gs.mw.c2[j];
 #pragma unroll
     for (int i = 0; i < kH; ++i) z = fmaf(gs.mw.w2[j * kH + i], h1[i], z);
-    const float h = sigmf(z);
-    gs.h2[tid][j] = h;
-    y = fmaf(gs.mw.w3[j], h, y);
+    h2v[jj] = sigmf(z);
+    gs.h2[q][j] = h2v[jj];
+    yp = fmaf(gs.mw.w3[j], h2v[jj], yp);
   }
-  // backward: e = dL/dy, d2 = dL/dz2, d1 = dL/dz1
-  const float r = y - t;
+  // the four threads of a point are adjacent lanes
+  yp += __shfl_xor_sync(kFull, yp, 1);
+  yp += __shfl_xor_sync(kFull, yp, 2);
+  const float r = yp + gs.mw.c3 - t;
   const float e = live ? 2.0f * r / (float)npts : 0.0f;
-  gs.e[tid] = e;
-  gs.x[tid] = x;
-  gs.se[tid] = live ? r * r : 0.0f;
-  float acc[kH];
-#pragma unroll
-  for (int i = 0; i < kH; ++i) acc[i] = 0.0f;
-  for (int j = 0; j < kH; ++j) {
-    const float h = gs.h2[tid][j];
-    const float d = e * gs.mw.w3[j] * h * (1.0f - h);
-    gs.d2[tid][j] = d;
-#pragma unroll
-    for (int i = 0; i < kH; ++i) acc[i] = fmaf(d, gs.mw.w2[j * kH + i], acc[i]);
+  if (part == 0) {
+    gs.e[q] = e;
+    gs.x[q] = x;
+    gs.se[q] = live ? r * r : 0.0f;
   }
+  // backward: d2 = dL/dz2 for this thread's units, then d1 = dL/dz1
 #pragma unroll
-  for (int i = 0; i < kH; ++i) {
-    gs.h1[tid][i] = h1[i];
-    gs.d1[tid][i] = acc[i] * h1[i] * (1.0f - h1[i]);
+  for (int jj = 0; jj < 8; ++jj) {
+    const int j = u0 + jj;
+    gs.d2[q][j] = e * gs.mw.w3[j] * h2v[jj] * (1.0f - h2v[jj]);
+  }
+  __syncthreads();
+#pragma unroll
+  for (int ii = 0; ii < 8; ++ii) {
+    const int i = u0 + ii;
+    float acc = 0.0f;
+#pragma unroll
+    for (int j = 0; j < kH; ++j) acc = fmaf(gs.d2[q][j], gs.mw.w2[j * kH + i], acc);
+    const float h = gs.h1[q][i];
+    gs.d1[q][i] = acc * h * (1.0f - h);
   }
   __syncthreads();
   // per-CTA gradient sums over its points, in point order
@@ -153,20 +168,20 @@ static __global__ void __launch_bounds__(kGradThreads) k_learn_step(LearnState* 
   for (int k = tid; k < kMlpParams + 1; k += kGradThreads) {
     float g = 0.0f;
     if (k < kOffC1) {
-      for (int q = 0; q < kGradThreads; ++q) g = fmaf(gs.d1[q][k], gs.x[q], g);
+      for (int p = 0; p < kGradPts; ++p) g = fmaf(gs.d1[p][k], gs.x[p], g);
     } else if (k < kOffV2) {
-      for (int q = 0; q < kGradThreads; ++q) g += gs.d1[q][k - kOffC1];
+      for (int p = 0; p < kGradPts; ++p) g += gs.d1[p][k - kOffC1];
     } else if (k < kOffC2) {
       const int j = (k - kOffV2) / kH, i = (k - kOffV2) % kH;
-      for (int q = 0; q < kGradThreads; ++q) g = fmaf(gs.d2[q][j], gs.h1[q][i], g);
+      for (int p = 0; p < kGradPts; ++p) g = fmaf(gs.d2[p][j], gs.h1[p][i], g);
     } else if (k < kOffV3) {
-      for (int q = 0; q < kGradThreads; ++q) g += gs.d2[q][k - kOffC2];
+      for (int p = 0; p < kGradPts; ++p) g += gs.d2[p][k - kOffC2];
     } else if (k < kOffC3) {
-      for (int q = 0; q < kGradThreads; ++q) g = fmaf(gs.e[q], gs.h2[q][k - kOffV3], g);
+      for (int p = 0; p < kGradPts; ++p) g = fmaf(gs.e[p], gs.h2[p][k - kOffV3], g);
     } else if (k == kOffC3) {
-      for (int q = 0; q < kGradThreads; ++q) g += gs.e[q];
+      for (int p = 0; p < kGradPts; ++p) g += gs.e[p];
     } else {
-      for (int q = 0; q < kGradThreads; ++q) g += gs.se[q];
+      for (int p = 0; p < kGradPts; ++p) g += gs.se[p];
     }
     out[k] = g;
   }
@@ -176,25 +191,33 @@ static __global__ void __launch_bounds__(kGradThreads) k_learn_step(LearnState* 
   __syncthreads();
   if (!gs.last) return;
   __threadfence();
+  const uint32_t nc = gridDim.x;
   for (int k = tid; k < kMlpParams + 1; k += kGradThreads) {
+    // L2 loads of the CTAs' sums, eight in flight at a time, added in CTA order
     float g = 0.0f;
-    for (uint32_t c = 0; c < gridDim.x; ++c) g += reinterpret_cast<volatile float*>(L->partial[c])[k];
+    for (uint32_t c0 = 0; c0 < nc; c0 += 8) {
+      float v[8];
+#pragma unroll
+      for (uint32_t u = 0; u < 8; ++u) v[u] = c0 + u < nc ? __ldcg(&L->partial[c0 + u][k]) : 0.0f;
+#pragma unroll
+      for (uint32_t u = 0; u < 8; ++u) g += v[u];
+    }
     if (k == kMlpParams) {
       L->grad[k] = g / (float)npts;  // mean squared error
       continue;
     }
-    const float q = L->p[k];
+    const float pk = L->p[k];
     // chain rule through the positivity transform: softplus' = sigmoid
-    if (k < kOffC1 || (k >= kOffV2 && k < kOffC2) || (k >= kOffV3 && k < kOffC3)) g *= sigmf(q);
+    if (k < kOffC1 || (k >= kOffV2 && k < kOffC2) || (k >= kOffV3 && k < kOffC3)) g *= sigmf(pk);
     L->grad[k] = g;
     if (step > 0) {
       const float m = 0.9f * L->m[k] + 0.1f * g;
-      const float v = 0.999f * L->v[k] + 0.001f * g * g;
+      const float vv = 0.999f * L->v[k] + 0.001f * g * g;
       L->m[k] = m;
-      L->v[k] = v;
+      L->v[k] = vv;
       const float mh = m / (1.0f - powf(0.9f, (float)step));
-      const float vh = v / (1.0f - powf(0.999f, (float)step));
-      L->p[k] = q - lr * mh / (sqrtf(vh) + 1e-8f);
+      const float vh = vv / (1.0f - powf(0.999f, (float)step));
+      L->p[k] = pk - lr * mh / (sqrtf(vh) + 1e-8f);
     }
   }
   if (tid == 0) L->done = 0;

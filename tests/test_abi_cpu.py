@@ -50,8 +50,8 @@ def test_workspace_size_and_argument_checks(lib):
     # n = 0 is valid and enqueues nothing
     rc = lib.semisort_equal(ss.SS_U64, ss.SS_U64, None, None, None, None, 0, None, 0, None, None)
     assert rc == 0
-    # misaligned pointers are rejected
-    rc = lib.semisort_equal(ss.SS_U64, ss.SS_U64, ctypes.c_void_p(8), ctypes.c_void_p(4096),
+    # pointers not aligned to their element size are rejected
+    rc = lib.semisort_equal(ss.SS_U64, ss.SS_U64, ctypes.c_void_p(12), ctypes.c_void_p(4096),
                             ctypes.c_void_p(1 << 20), ctypes.c_void_p(1 << 21), 4, ctypes.c_void_p(1 << 22),
                             1 << 30, None, None)
     assert rc == 1
