@@ -174,6 +174,8 @@ ss_status make_plan(int op, int kt, int vt, uint64_t n, const ss_options* opt, i
   o = al(o + (wide && multi ? (size_t)kBigSample * P->kbytes : 0));
   P->off_learn = o;
   o = al(o + (wide && multi ? sizeof(LearnState) : 0));
+  P->off_toptab = o;
+  o = al(o + (wide && multi ? sizeof(TopTable) : 0));
   P->off_inst_base = o;
   o = al(o + (batched && red ? (size_t)5 * num_inst * 8 : 0));
   P->off_inst_first = o;
@@ -222,6 +224,7 @@ void fill_work(const Plan& P, void* ws, Work* w) {
   w->bigs = b + P.off_bigs;
   w->bigs_tmp = b + P.off_bigs_tmp;
   w->learn = b + P.off_learn;
+  w->toptab = reinterpret_cast<TopTable*>(b + P.off_toptab);
   w->inst_base = reinterpret_cast<uint64_t*>(b + P.off_inst_base);
   w->inst_first = reinterpret_cast<uint64_t*>(b + P.off_inst_first);
   w->num_inst = P.num_inst > 0 ? P.num_inst : 1;

@@ -112,6 +112,26 @@ __device__ __forceinline__ uint32_t bucket_less(const K& k, const K* bnd, const 
   return 2 * lo;
 }
 
+// semisort_< bucket through the top level's lookup table: the boundaries
+// that can order a key are those of its cell, so the search covers only them.
+template <class K>
+__device__ __forceinline__ uint32_t bucket_less_tab(const K& k, const K* bnd, const uint16_t* flags,
+                                                    const uint16_t* cell, uint64_t kmin, uint32_t shift) {
+  const uint64_t kk = (uint64_t)k;
+  uint64_t c = kk > kmin ? (kk - kmin) >> shift : 0;
+  c = c < kTopCells - 1 ? c : kTopCells - 1;
+  uint32_t lo = cell[c], hi = cell[c + 1];
+  while (lo < hi) {
+    const uint32_t mid = (lo + hi) >> 1;
+    if (KeyT<K>::lt(k, bnd[mid]))
+      hi = mid;
+    else
+      lo = mid + 1;
+  }
+  if (lo > 0 && flags[lo - 1] && KeyT<K>::eq(bnd[lo - 1], k)) return 2 * lo - 1;
+  return 2 * lo;
+}
+
 // Whether the semisort_< top level uses the wide bucket space (2^16-key
 // sample, up to 2^11 ranges): for keys up to 8 bytes, whose wide distribute
 // buffers fit in shared memory.
@@ -629,6 +649,36 @@ __global__ void __launch_bounds__(1024) k_less_split(Work w, const LearnState* L
     bnd[u] = bs[u];
     fl[u] = fs[u];
   }
+  // lookup table: cells of 2^shift keys from the sample minimum, 4096 cells
+  // spanning the sample's key range; cell[c] = boundaries below cell c's start
+  {
+    const uint64_t kmin = (uint64_t)S[0], range = (uint64_t)S[kBigSample - 1] - kmin;
+    const uint32_t bits = range ? 64 - __clzll((long long)range) : 0;
+    const uint32_t shift = bits > 12 ? bits - 12 : 0;
+    TopTable* T = w.toptab;
+    for (uint32_t c = threadIdx.x; c <= kTopCells; c += blockDim.x) {
+      uint32_t lo = 0;
+      if (c == kTopCells || (c > 0 && ((uint64_t)c << shift) > ~0ull - kmin)) {
+        lo = q;
+      } else if (c > 0) {
+        const uint64_t start = kmin + ((uint64_t)c << shift);  // first key of cell c
+        uint32_t hi = q;
+        while (lo < hi) {
+          const uint32_t mid = (lo + hi) >> 1;
+          if ((uint64_t)bs[mid] < start)
+            lo = mid + 1;
+          else
+            hi = mid;
+        }
+      }
+      T->cell[c] = (uint16_t)lo;
+    }
+    if (threadIdx.x == 0) {
+      T->kmin = kmin;
+      T->shift = shift;
+      T->q = q;
+    }
+  }
   if (threadIdx.x == 0) {
     sgp[0].nh = q;
     sgp[0].nb = 2 * q + 1;
@@ -687,7 +737,18 @@ struct CountSmem {
   K hk[Space<BIG>::kBnd];
   uint16_t ht[Space<BIG>::kTab];
   unsigned long long hsum[OP == kOpReduce ? kMaxHeavy : 1];
+  uint16_t cell[BIG ? kTopCells + 1 : 1];
 };
+
+// The wide top level's lookup table into shared memory.
+template <bool BIG>
+__device__ __forceinline__ void load_cells(const Work& w, uint16_t* cell, uint64_t* kmin, uint32_t* shift) {
+  if constexpr (BIG) {
+    for (uint32_t i = threadIdx.x; i <= kTopCells; i += blockDim.x) cell[i] = w.toptab->cell[i];
+    *kmin = w.toptab->kmin;
+    *shift = w.toptab->shift;
+  }
+}
 
 template <class K, class V, int OP, bool BIG>
 __global__ void __launch_bounds__(kCountThreads) k_count(Work w, LevelBufs lb) {
@@ -705,6 +766,9 @@ __global__ void __launch_bounds__(kCountThreads) k_count(Work w, LevelBufs lb) {
     const uint32_t nb = sg.nb;
     const uint32_t tmask = 4 * hcap_of(sg.lbits) - 1;
     load_heavy<K, OP>(w, lb.level, sg, hk, ht);
+    uint64_t tkmin = 0;
+    uint32_t tshift = 0;
+    load_cells<BIG && OP == kOpLess>(w, cs.cell, &tkmin, &tshift);
     for (uint32_t b = threadIdx.x; b < nb; b += blockDim.x) hist[b] = 0;
     if (OP == kOpReduce)
       for (uint32_t b = threadIdx.x; b < sg.nh; b += blockDim.x) hsum[b] = 0;
@@ -722,7 +786,11 @@ __global__ void __launch_bounds__(kCountThreads) k_count(Work w, LevelBufs lb) {
       for (int u = 0; u < U; ++u) {
         const uint32_t i = i0 + u * blockDim.x + threadIdx.x;
         if (i < tl.len) {
-          const uint32_t b = bucket_in<K, OP>(key[u], sg, hk, ht, tmask);
+          uint32_t b;
+          if constexpr (BIG && OP == kOpLess)
+            b = bucket_less_tab<K>(key[u], hk, ht, cs.cell, tkmin, tshift);
+          else
+            b = bucket_in<K, OP>(key[u], sg, hk, ht, tmask);
           atomicAdd(&hist[b], 1u);
           if constexpr (OP == kOpReduce) {
             if (b >= nl) {
@@ -931,6 +999,7 @@ struct DistSmem {
   uint32_t cur[Space<BIG>::kIds];    // next write offset per bucket within the segment
   K hk[Space<BIG>::kBnd];
   uint16_t ht[Space<BIG>::kTab];
+  uint16_t cell[BIG ? kTopCells + 1 : 1];
 };
 
 // Record i of a level's source (caller SoA at level 0, AoS records after).
@@ -987,6 +1056,9 @@ __global__ void __launch_bounds__(kDT, 2) k_distribute(Work w, LevelBufs lb) {
     const uint32_t nb = sg.nb;
     const uint32_t tmask = 4 * hcap_of(sg.lbits) - 1;
     load_heavy<K, OP>(w, lb.level, sg, sm.hk, sm.ht);
+    uint64_t tkmin = 0;
+    uint32_t tshift = 0;
+    load_cells<BIG && OP == kOpLess>(w, sm.cell, &tkmin, &tshift);
     {
       const uint32_t* X = w.C[lb.level] + sg.cbase;
       const uint32_t* boff = w.boff[lb.level] + sg.bbase;
@@ -1002,8 +1074,15 @@ __global__ void __launch_bounds__(kDT, 2) k_distribute(Work w, LevelBufs lb) {
       // invalid slots get id 2^15 - 1: every 5-bit digit is 31, and as the last
       // items in blocked order they rank after every valid record
 #pragma unroll
-      for (int r = 0; r < kDR; ++r)
-        bid[r] = c0t + r < clen ? bucket_in<K, OP>(sm.S[sw<RB>(c0t + r)].k, sg, sm.hk, sm.ht, tmask) : 0x7FFFu;
+      for (int r = 0; r < kDR; ++r) {
+        if (c0t + r >= clen) {
+          bid[r] = 0x7FFFu;
+        } else if constexpr (BIG && OP == kOpLess) {
+          bid[r] = bucket_less_tab<K>(sm.S[sw<RB>(c0t + r)].k, sm.hk, sm.ht, sm.cell, tkmin, tshift);
+        } else {
+          bid[r] = bucket_in<K, OP>(sm.S[sw<RB>(c0t + r)].k, sg, sm.hk, sm.ht, tmask);
+        }
+      }
       DRank::rank(sm.rk, bid, 0, rk);
 #pragma unroll
       for (int r = 0; r < kDR; ++r) sm.px[bpad(rk[r])] = (bid[r] << 16) | (c0t + r);
@@ -1363,35 +1442,44 @@ __global__ void __launch_bounds__(kRT, 2) k_finish_equal(Work w) {
 }
 
 // ----------------------------------------------------------------------------
-// finish (semisort_<): the base case of Sec. 3.3 with a comparison sort, and
-// the copy-backs of Sec. 3.4.  A window is sorted in shared memory by (key,
-// position in the window) with Batcher's bitonic network; only 16-bit
-// positions move, keys stay where they were loaded.  The position tie-break
-// makes the order stable, so the output equals a stable sort by key.
+// finish (semisort_<): the base case of Sec. 3.3 with a sort by key, and the
+// copy-backs of Sec. 3.4.  A window's records are staged once in shared
+// memory.  For keys up to 8 bytes every record gets an interpolation bucket,
+// the top 12 bits of (key - window minimum), a non-decreasing function of the
+// key; a stable rank by it (at most three 5-bit passes) leaves the window
+// ordered by bucket with input order inside each bucket, and an insertion sort
+// (stable) finishes every run of equal buckets.  Runs are short unless keys
+// repeat (then they are already in order) or cluster; a window with a long
+// unordered run -- and every window of 128-bit keys -- is sorted instead by
+// Batcher's bitonic network on (key, position in the window).  Either way the
+// output is the stable sort of the window.
 // ----------------------------------------------------------------------------
 template <class K, class V>
 struct LessSmem {
+  RecT<K, V> S[kRefMax];  // the window, swizzled (sw)
   union {
-    struct {
-      K keys[kRefMax];
-      uint16_t idx[kRefMax];
-    } s;
-    RecT<K, V> stage[kRefMax];
+    typename RRank::Smem rk;
+    uint16_t idx[kRefMax];  // bitonic: positions in the window
   } u;
-  uint16_t fpos[kRefMax];
+  uint32_t px[kRefMax + kRefMax / 32];  // (bucket << 16 | index) at rank, padded (bpad)
+  uint32_t scan_tmp[33];
+  unsigned long long mn[32], mx[32];
+  uint32_t fallback;
 };
 
 template <class K, class V>
 __global__ void __launch_bounds__(kRT, 2) k_finish_less(Work w) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
   LessSmem<K, V>& sm = *reinterpret_cast<LessSmem<K, V>*>(smem_raw);
+  using Rec = RecT<K, V>;
+  constexpr int RB = sizeof(Rec);
   const uint32_t nfin = w.ctrl->nfin;
-  const int tid = threadIdx.x;
+  const int tid = threadIdx.x, lane = tid & 31, wid = tid >> 5;
+  const uint32_t c0t = tid * kRR;
   for (uint32_t itx = blockIdx.x; itx < nfin; itx += gridDim.x) {
     const Item it = w.items[itx];
     if (it.kind == kItemCopy) {
-      for (uint32_t i = tid; i < it.len; i += kRT)
-        store_out<K, V>(w, it.start + i, load_rec<K, V>(w, it.buf, it.start + i));
+      copy_item<kRT, K, V>(w, it);
       if (tid == 0) atomicAdd((unsigned long long*)&w.ctrl->stats[6], (unsigned long long)it.len);
       continue;
     }
@@ -1400,46 +1488,131 @@ __global__ void __launch_bounds__(kRT, 2) k_finish_less(Work w) {
       if (tid == 0) set_error(w.ctrl, 8);
       continue;
     }
-    uint32_t P = 2;
-    while (P < m) P <<= 1;
-    for (uint32_t c = tid; c < P; c += kRT) {
-      if (c < m)
-        sm.u.s.keys[c] = it.buf == kBufIn ? reinterpret_cast<const K*>(w.in_k)[it.start + c]
-                                          : reinterpret_cast<const RecT<K, V>*>(buf_ptr(w, it.buf))[it.start + c].k;
-      sm.u.s.idx[c] = (uint16_t)c;  // positions >= m are padding and order after every record
-    }
+    load_chunk<kRT, K, V>(sm.S, m, [&](uint32_t i) { return load_rec<K, V>(w, it.buf, it.start + i); });
     if (tid == 0) {
+      sm.fallback = sizeof(K) > 8 ? 1u : 0u;
       atomicAdd((unsigned long long*)&w.ctrl->stats[5], (unsigned long long)m);
       atomicAdd((unsigned long long*)&w.ctrl->stats[9], 1ull);
       atomicMax((unsigned long long*)&w.ctrl->stats[8], (unsigned long long)m);
     }
+    __syncthreads();
+    if constexpr (sizeof(K) <= 8) {
+      // key range of the window
+      unsigned long long lo = ~0ull, hi = 0;
+#pragma unroll
+      for (int r = 0; r < kRR; ++r) {
+        if (c0t + r < m) {
+          const unsigned long long k = (uint64_t)sm.S[sw<RB>(c0t + r)].k;
+          lo = k < lo ? k : lo;
+          hi = k > hi ? k : hi;
+        }
+      }
+#pragma unroll
+      for (int o = 16; o > 0; o >>= 1) {
+        const unsigned long long a = __shfl_xor_sync(kFull, lo, o), b = __shfl_xor_sync(kFull, hi, o);
+        lo = a < lo ? a : lo;
+        hi = b > hi ? b : hi;
+      }
+      if (lane == 0) {
+        sm.mn[wid] = lo;
+        sm.mx[wid] = hi;
+      }
+      __syncthreads();
+      lo = ~0ull;
+      hi = 0;
+      for (int i = 0; i < kRT / 32; ++i) {
+        lo = sm.mn[i] < lo ? sm.mn[i] : lo;
+        hi = sm.mx[i] > hi ? sm.mx[i] : hi;
+      }
+      const uint64_t range = hi - lo;
+      const uint32_t bits = range ? 64 - __clzll((long long)range) : 0;
+      const uint32_t shift = bits > 12 ? bits - 12 : 0;
+      const uint32_t nbits = bits - shift;  // bucket ids < 2^nbits <= 4096
+      if (nbits == 0) {
+        // all keys equal: the window is already sorted
+        for (uint32_t p = tid; p < m; p += kRT) store_out<K, V>(w, it.start + p, sm.S[sw<RB>(p)]);
+        __syncthreads();
+        continue;
+      }
+      uint32_t g[kRR], rk[kRR];
+#pragma unroll
+      for (int r = 0; r < kRR; ++r) {
+        const uint32_t c = c0t + r;
+        const uint32_t ib = c < m ? (uint32_t)(((uint64_t)sm.S[sw<RB>(c)].k - lo) >> shift) : 0x7FFFu;
+        g[r] = (ib << 16) | c;
+      }
+      const uint32_t passes = (nbits + 4) / 5;
+      for (uint32_t pz = 0; pz < passes; ++pz) {
+        RRank::rank(sm.u.rk, g, 16 + 5 * pz, rk);
+#pragma unroll
+        for (int r = 0; r < kRR; ++r) sm.px[bpad(rk[r])] = g[r];
+        __syncthreads();
+        if (pz + 1 < passes) {
+#pragma unroll
+          for (int r = 0; r < kRR; ++r) g[r] = sm.px[bpad(c0t + r)];
+        }
+      }
+      // finish every run of equal buckets by a stable insertion sort on the key
+      auto key_at = [&](uint32_t x) { return sm.S[sw<RB>(x & 0xFFFFu)].k; };
+      for (uint32_t p = tid; p < m; p += kRT) {
+        const uint32_t b = sm.px[bpad(p)] >> 16;
+        if (p > 0 && (sm.px[bpad(p - 1)] >> 16) == b) continue;  // not a run start
+        uint32_t e = p + 1;
+        while (e < m && (sm.px[bpad(e)] >> 16) == b) ++e;
+        if (e - p < 2) continue;
+        if (e - p > 64) {
+          bool sorted = true;
+          for (uint32_t i = p + 1; i < e && sorted; ++i)
+            sorted = !KeyT<K>::lt(key_at(sm.px[bpad(i)]), key_at(sm.px[bpad(i - 1)]));
+          if (!sorted) sm.fallback = 1;
+          continue;
+        }
+        for (uint32_t i = p + 1; i < e; ++i) {
+          const uint32_t x = sm.px[bpad(i)];
+          const K kx = key_at(x);
+          uint32_t j = i;
+          while (j > p && KeyT<K>::lt(kx, key_at(sm.px[bpad(j - 1)]))) {
+            sm.px[bpad(j)] = sm.px[bpad(j - 1)];
+            --j;
+          }
+          sm.px[bpad(j)] = x;
+        }
+      }
+      __syncthreads();
+      if (!sm.fallback) {
+        for (uint32_t p = tid; p < m; p += kRT)
+          store_out<K, V>(w, it.start + p, sm.S[sw<RB>(sm.px[bpad(p)] & 0xFFFFu)]);
+        __syncthreads();
+        continue;
+      }
+    }
+    // bitonic network on (key, position), positions only move
+    uint32_t P = 2;
+    while (P < m) P <<= 1;
+    for (uint32_t c = tid; c < P; c += kRT) sm.u.idx[c] = (uint16_t)c;  // positions >= m: padding, last
     __syncthreads();
     for (uint32_t k = 2; k <= P; k <<= 1) {
       for (uint32_t j = k >> 1; j > 0; j >>= 1) {
         for (uint32_t p = tid; p < P / 2; p += kRT) {
           const uint32_t i = ((p & ~(j - 1)) << 1) | (p & (j - 1));
           const uint32_t ixj = i + j;
-          const uint32_t ia = sm.u.s.idx[i], ib = sm.u.s.idx[ixj];
+          const uint32_t ia = sm.u.idx[i], ib = sm.u.idx[ixj];
           bool gt;  // (key, position) of slot i above that of slot i + j
           if (ia >= m || ib >= m) {
             gt = ia > ib;
           } else {
-            const K ka = sm.u.s.keys[ia], kb = sm.u.s.keys[ib];
+            const K ka = sm.S[sw<RB>(ia)].k, kb = sm.S[sw<RB>(ib)].k;
             gt = KeyT<K>::lt(kb, ka) || (KeyT<K>::eq(ka, kb) && ia > ib);
           }
           if (gt == ((i & k) == 0)) {
-            sm.u.s.idx[i] = (uint16_t)ib;
-            sm.u.s.idx[ixj] = (uint16_t)ia;
+            sm.u.idx[i] = (uint16_t)ib;
+            sm.u.idx[ixj] = (uint16_t)ia;
           }
         }
         __syncthreads();
       }
     }
-    for (uint32_t p = tid; p < m; p += kRT) sm.fpos[sm.u.s.idx[p]] = (uint16_t)p;
-    __syncthreads();  // keys and positions are dead: the region becomes the staging buffer
-    for (uint32_t c = tid; c < m; c += kRT) sm.u.stage[sm.fpos[c]] = load_rec<K, V>(w, it.buf, it.start + c);
-    __syncthreads();
-    for (uint32_t p = tid; p < m; p += kRT) store_out<K, V>(w, it.start + p, sm.u.stage[p]);
+    for (uint32_t p = tid; p < m; p += kRT) store_out<K, V>(w, it.start + p, sm.S[sw<RB>(sm.u.idx[p])]);
     __syncthreads();
   }
 }

@@ -30,6 +30,18 @@ enum Op : int { kOpEqual = 0, kOpLess = 1, kOpReduce = 2, kOpHist = 3 };
 // Buffer ids used by work items.
 enum Buf : uint32_t { kBufIn = 0, kBufT = 1, kBufOut = 2, kBufT2 = 3 };
 
+// Lookup table of the wide semisort_< top level: boundary search ranges per
+// key cell.  Cell c covers the keys kmin + [c, c + 1) * 2^shift (keys below kmin
+// fall in cell 0, keys above the last cell in cell kTopCells - 1); boundaries
+// cell[c] .. cell[c + 1] - 1 lie inside cell c.
+constexpr uint32_t kTopCells = 4096;
+struct TopTable {
+  uint64_t kmin;
+  uint32_t shift;
+  uint32_t q;
+  uint16_t cell[kTopCells + 1];
+};
+
 // Finish items of a batched call's instances of at most alpha records carry
 // this level tag (they go straight to the base case).
 constexpr uint32_t kDirectLevel = kMaxLevels;
@@ -128,6 +140,7 @@ struct Work {
   void* bigs;           // semisort_<: the sorted top-level sample (kBigSample keys)
   void* bigs_tmp;       // its sorted runs before the merge
   void* learn;          // semisort_<: learned-splitter state (LearnState)
+  TopTable* toptab;     // semisort_<: lookup table of the wide top level
   uint32_t splitter_mode;  // 0 sampled, 1 learned (semisort_< top level)
   // batched calls: instance i holds records [offsets[i], offsets[i+1])
   const uint64_t* offsets;  // device, num_inst + 1 entries; null for a single instance
@@ -154,7 +167,7 @@ struct Plan {
       off_htab[kMaxLevels], off_bsize[kMaxLevels], off_boff[kMaxLevels], off_hpart[kMaxLevels],
       off_split[kMaxLevels];
   size_t off_items, off_item_out, off_item_pos, off_block_sums, off_ctrl, off_scratch32, off_item_aux;
-  size_t off_bigs, off_bigs_tmp, off_learn, off_inst_base, off_inst_first;
+  size_t off_bigs, off_bigs_tmp, off_learn, off_inst_base, off_inst_first, off_toptab;
   uint32_t num_inst;
   size_t total;
 };

@@ -135,3 +135,16 @@ def test_parameters(ss, alpha, subarray, lbits):
     vals = np.arange(n, dtype=np.uint64)
     ko, vo, _ = run_less(ss, keys, vals, alpha=alpha, subarray=subarray, n_light_log2=lbits)
     check(keys, vals, ko, vo)
+
+
+@pytest.mark.parametrize("n", [3000, 1 << 20])
+def test_clustered_keys(ss, n):
+    """Far outliers stretch the key range so that clustered keys share one
+    interpolation bucket of their window: the base case must still sort them."""
+    rng = np.random.default_rng(n)
+    keys = rng.integers(1000, 1000 + 4 * n, size=n, dtype=np.uint64)
+    keys[::97] = np.uint64(2**63) + rng.integers(0, 10, size=len(keys[::97]), dtype=np.uint64)
+    keys[5] = np.uint64(2**64 - 1)
+    vals = np.arange(n, dtype=np.uint64)
+    ko, vo, _ = run_less(ss, keys, vals)
+    check(keys, vals, ko, vo)
