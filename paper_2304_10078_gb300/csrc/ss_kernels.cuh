@@ -736,7 +736,10 @@ struct CountSmem {
   uint32_t hist[Space<BIG>::kIds];
   K hk[Space<BIG>::kBnd];
   uint16_t ht[Space<BIG>::kTab];
-  unsigned long long hsum[OP == kOpReduce ? kMaxHeavy : 1];
+  // collect-reduce: per-subarray sums of the heavy keys' values, eight copies
+  // per key (picked by lane) so that a warp's records of one key collide at
+  // most four ways in the shared-memory atomics
+  unsigned long long hsum[OP == kOpReduce ? kMaxHeavy * 8 : 1];
   uint16_t cell[BIG ? kTopCells + 1 : 1];
 };
 
@@ -771,7 +774,7 @@ __global__ void __launch_bounds__(kCountThreads) k_count(Work w, LevelBufs lb) {
     load_cells<BIG && OP == kOpLess>(w, cs.cell, &tkmin, &tshift);
     for (uint32_t b = threadIdx.x; b < nb; b += blockDim.x) hist[b] = 0;
     if (OP == kOpReduce)
-      for (uint32_t b = threadIdx.x; b < sg.nh; b += blockDim.x) hsum[b] = 0;
+      for (uint32_t b = threadIdx.x; b < sg.nh * 8; b += blockDim.x) hsum[b] = 0;
     __syncthreads();
     constexpr int U = 4;
     const uint32_t per = blockDim.x * U;
@@ -799,7 +802,7 @@ __global__ void __launch_bounds__(kCountThreads) k_count(Work w, LevelBufs lb) {
                 v = (uint64_t)reinterpret_cast<const RecT<K, uint64_t>*>(lb.src_k)[tl.start + i].v;
               else
                 v = reinterpret_cast<const uint64_t*>(lb.src_v)[tl.start + i];
-              atomicAdd(&hsum[b - nl], (unsigned long long)v);
+              atomicAdd(&hsum[(b - nl) * 8 + (threadIdx.x & 7)], (unsigned long long)v);
             }
           }
         }
@@ -810,7 +813,12 @@ __global__ void __launch_bounds__(kCountThreads) k_count(Work w, LevelBufs lb) {
     for (uint32_t b = threadIdx.x; b < nb; b += blockDim.x) C[(uint64_t)b * sg.ntiles + tl.idx] = hist[b];
     if (OP == kOpReduce) {
       uint64_t* HP = w.hpart[lb.level] + sg.cbase;
-      for (uint32_t b = threadIdx.x; b < sg.nh; b += blockDim.x) HP[(uint64_t)b * sg.ntiles + tl.idx] = hsum[b];
+      for (uint32_t b = threadIdx.x; b < sg.nh; b += blockDim.x) {
+        unsigned long long t = 0;
+#pragma unroll
+        for (int c = 0; c < 8; ++c) t += hsum[b * 8 + c];
+        HP[(uint64_t)b * sg.ntiles + tl.idx] = t;
+      }
     }
     __syncthreads();
   }
@@ -1086,15 +1094,19 @@ __global__ void __launch_bounds__(kDT, 2) k_distribute(Work w, LevelBufs lb) {
       DRank::rank(sm.rk, bid, 0, rk);
 #pragma unroll
       for (int r = 0; r < kDR; ++r) sm.px[bpad(rk[r])] = (bid[r] << 16) | (c0t + r);
-      for (int pz = 1; pz < passes; ++pz) {
+      // further passes as straight-line code with constant digit positions
+      // (a loop over passes would keep the arrays in local memory)
+      auto pass = [&](int shift) {
         __syncthreads();
         uint32_t x[kDR];
 #pragma unroll
         for (int r = 0; r < kDR; ++r) x[r] = sm.px[bpad(c0t + r)];
-        DRank::rank(sm.rk, x, 16 + 5 * pz, rk);
+        DRank::rank(sm.rk, x, shift, rk);
 #pragma unroll
         for (int r = 0; r < kDR; ++r) sm.px[bpad(rk[r])] = x[r];
-      }
+      };
+      if (passes > 1) pass(21);
+      if (BIG && passes > 2) pass(26);
       __syncthreads();
       // run starts: turn the bucket's running offset into the base of this chunk
       for (uint32_t p = tid; p < clen; p += kDT) {
