@@ -347,6 +347,81 @@ def bench_batched(ss, sg, torch, stream, reps=3):
     return res
 
 
+RMAT_SEED = 0x5EED0005
+
+
+def rmat_partitions(m, parts=64):
+    """Contiguous edge ranges with seeded log-uniform sizes 2^U[0,4], scaled to m."""
+    import numpy as np
+
+    import synth
+    w = 2.0 ** (4.0 * synth.unit(synth.rand64(RMAT_SEED, 0x9A, np.arange(parts, dtype=np.uint64))))
+    cut = np.floor(np.cumsum(w) / w.sum() * m).astype(np.int64)
+    cut[-1] = m
+    return np.concatenate([[0], cut]).astype(np.int64)
+
+
+def bench_rmat_csr(ss, sg, torch, stream, reps=3, scale=26, m=1 << 30):
+    """CSR build of an R-MAT graph (2^26 vertices, 2^30 edges, u32 src / u32
+    dst) over 64 uneven edge partitions: semisort_< on src with dst as value
+    plus the degree histogram.  One batched call of each, against one call
+    per partition (sampled splitters) and per partition with learned
+    splitters.  Records = edges."""
+    import numpy as np
+    src, dst = sg.rmat_edges(RMAT_SEED, m, scale)
+    off_h = rmat_partitions(m)
+    parts = len(off_h) - 1
+    off = torch.from_numpy(off_h).cuda().view(torch.uint64)
+    ks, vs = torch.empty_like(src), torch.empty_like(dst)
+    uk = torch.empty_like(src)
+    cnt = torch.empty(m, dtype=torch.uint32, device="cuda")
+    nu = torch.zeros(parts, dtype=torch.uint64, device="cuda")
+    oo = torch.zeros(parts + 1, dtype=torch.uint64, device="cuda")
+    plain = ss.make_options(seed=1)
+    ws_l = ss.alloc_workspace_batched(ss.OP_LESS, src, off, dst, plain)
+    ws_h = ss.alloc_workspace_batched(ss.OP_HIST, src, off, None, plain)
+
+    def batched():
+        ss.semisort_less_batched(src, dst, off, keys_out=ks, vals_out=vs, workspace=ws_l, options=plain)
+        ss.histogram_batched(src, off, capacity=m, ukeys_out=uk, counts_out=cnt, num_unique=nu, out_offsets=oo,
+                             workspace=ws_h, options=plain)
+
+    def timed(fn, k):
+        fn()
+        a = torch.cuda.Event(enable_timing=True)
+        b = torch.cuda.Event(enable_timing=True)
+        a.record(stream)
+        for _ in range(k):
+            fn()
+        b.record(stream)
+        b.synchronize()
+        return a.elapsed_time(b) / k
+
+    t_b = timed(batched, reps)
+    assert ss.last_device_error(ws_l) == 0 and ss.last_device_error(ws_h) == 0
+    del ws_l, ws_h
+    big = int(np.max(np.diff(off_h)))
+    learned = ss.make_options(seed=1, splitter_mode=1)
+    w1l = ss.alloc_workspace(ss.OP_LESS, src[:big], dst[:big], learned)
+    w1h = ss.alloc_workspace(ss.OP_HIST, src[:big], None, plain)
+    nu1 = torch.zeros(1, dtype=torch.uint64, device="cuda")
+    out = {}
+    for mode, opt in (("per_partition_sampled", plain), ("per_partition_learned", learned)):
+        def per_part():
+            for p in range(parts):
+                a, b = int(off_h[p]), int(off_h[p + 1])
+                ss.semisort_less(src[a:b], dst[a:b], keys_out=ks[a:b], vals_out=vs[a:b], workspace=w1l, options=opt)
+                ss.histogram(src[a:b], capacity=b - a, ukeys_out=uk[a:b], counts_out=cnt[a:b], num_unique=nu1,
+                             workspace=w1h, options=plain)
+        out[mode] = timed(per_part, 1)
+        assert ss.last_device_error(w1l) == 0
+    return {"workload": f"R-MAT scale {scale}, {m} edges (u32 src, u32 dst), 64 partitions of sizes 2^U[0,4]",
+            "unit": UNIT, "batched": m / (t_b / 1000) / 1e9,
+            "per_partition_sampled": m / (out["per_partition_sampled"] / 1000) / 1e9,
+            "per_partition_learned": m / (out["per_partition_learned"] / 1000) / 1e9,
+            "ms": {"batched": t_b, **out}}
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -359,7 +434,7 @@ def main():
     ap.add_argument("--e2e-steps", type=int, default=3)
     ap.add_argument("--quick", action="store_true", help="small smoke configuration (not a bench number)")
     ap.add_argument("--dists", default="", help="comma-separated indices into the distribution list")
-    ap.add_argument("--ops", default="collect_reduce,histogram,semisort_less,semisort_less_learned,batched",
+    ap.add_argument("--ops", default="collect_reduce,histogram,semisort_less,semisort_less_learned,batched,rmat_csr",
                     help="further operations timed after the headline (empty: none)")
     args = ap.parse_args()
 
@@ -489,11 +564,15 @@ def main():
     for o in ops:
         if o != "batched":
             by_op[o] = time_op(ss, sg, torch, o, keys, dists, vals, kout, vout, ws, n, stream)
-    if "batched" in ops:
+    if "batched" in ops or "rmat_csr" in ops:
         keys.clear()
         del ws, kout, vout, vals
         torch.cuda.empty_cache()
+    if "batched" in ops:
         by_op["batched"] = bench_batched(ss, sg, torch, stream, reps=3)
+        torch.cuda.empty_cache()
+    if "rmat_csr" in ops:
+        by_op["rmat_csr"] = bench_rmat_csr(ss, sg, torch, stream, reps=3)
 
     if rank != 0:
         if world > 1:
