@@ -184,7 +184,9 @@ def time_op(ss, sg, torch, name, keys, dists, vals, kout, vout, ws, n, stream):
     semisort_< on uniform-10^9, Zipf-1.2, floor(Exp(10^-6)) and an 8-component
     Gaussian mixture."""
     learned = name == "semisort_less_learned"
-    opt = ss.make_options(seed=1, flags=ss.FLAG_PHASE_TIMING, splitter_mode=1 if learned else 0)
+    flags = ss.FLAG_PHASE_TIMING | (ss.FLAG_IDENTITY_HASH if name == "semisort_equal_identity" else 0) | \
+        (ss.FLAG_HASH_BUCKETS if name == "semisort_less_hash" else 0)
+    opt = ss.make_options(seed=1, flags=flags, splitter_mode=1 if learned else 0)
     nu = torch.zeros(1, dtype=torch.uint64, device="cuda")
     names = [dist_name(d) for d in dists]
     inputs = list(keys)
@@ -200,7 +202,7 @@ def time_op(ss, sg, torch, name, keys, dists, vals, kout, vout, ws, n, stream):
             names.append(f"{kind}-{p:g}")
 
     def call(k):
-        if name == "semisort_equal":
+        if name.startswith("semisort_equal"):
             ss.semisort_equal(k, vals, keys_out=kout, vals_out=vout, workspace=ws, options=opt)
         elif name.startswith("semisort_less"):
             ss.semisort_less(k, vals, keys_out=kout, vals_out=vout, workspace=ws, options=opt)
@@ -225,7 +227,7 @@ def time_op(ss, sg, torch, name, keys, dists, vals, kout, vout, ws, n, stream):
         total += per[nm]
         for pn, pm in ss.phase_times():
             phases[pn] = phases.get(pn, 0.0) + pm / len(inputs)
-        if name.startswith("semisort_less"):
+        if name in ("semisort_less", "semisort_less_learned"):
             st = ss.stats(ws)
             balance[nm] = {"splitters": ["sampled", "learned", "learned rejected"][st["l0_splitters"]],
                            "max_light_bucket_over_mean": st["l0_max_light_bucket"] / (n / 2048.0),
@@ -434,7 +436,8 @@ def main():
     ap.add_argument("--e2e-steps", type=int, default=3)
     ap.add_argument("--quick", action="store_true", help="small smoke configuration (not a bench number)")
     ap.add_argument("--dists", default="", help="comma-separated indices into the distribution list")
-    ap.add_argument("--ops", default="collect_reduce,histogram,semisort_less,semisort_less_learned,batched,rmat_csr",
+    ap.add_argument("--ops", default="collect_reduce,histogram,semisort_equal_identity,semisort_less,"
+                                      "semisort_less_learned,semisort_less_hash,batched,rmat_csr",
                     help="further operations timed after the headline (empty: none)")
     args = ap.parse_args()
 
@@ -468,7 +471,8 @@ def main():
     opt = ss.make_options(seed=1, flags=ss.FLAG_PHASE_TIMING)
     ops = [o for o in args.ops.split(",") if o]
     op_codes = {"semisort_equal": ss.OP_EQUAL, "collect_reduce": ss.OP_REDUCE, "histogram": ss.OP_HIST,
-                "semisort_less": ss.OP_LESS, "semisort_less_learned": ss.OP_LESS}
+                "semisort_less": ss.OP_LESS, "semisort_less_learned": ss.OP_LESS, "semisort_less_hash": ss.OP_LESS,
+                "semisort_equal_identity": ss.OP_EQUAL}
     ws_bytes = max(ss.workspace_size(op_codes[o], ss.SS_U64, ss.SS_U64, n, opt)
                    for o in ["semisort_equal"] + ops if o in op_codes)
     ws = torch.empty(ws_bytes, dtype=torch.uint8, device="cuda")

@@ -85,7 +85,17 @@ typedef struct {
 } ss_options;
 
 #define SS_FLAG_PHASE_TIMING 0x1 /* record per-kernel CUDA events (ss_phase_times) */
-#define SS_FLAG_IDENTITY_HASH 0x2 /* integer keys hashed by identity (Sec. 4.1 "-i") */
+/* Integer keys (u32, u64) bucketed by their own bits instead of a hash: the
+ * lowest bits at the top level, the next ones at each deeper level (the
+ * "-i" variants of Sec. 4.1).  Same results; fast for keys whose low bits are
+ * spread, slow (deep recursion, SS_ERR_DEPTH) for keys that share them.
+ * Ignored for 128-bit keys and by semisort_< with range buckets. */
+#define SS_FLAG_IDENTITY_HASH 0x2
+/* semisort_less only: the paper's semisort_< -- hash buckets (as
+ * semisort_equal) whose base cases are sorted by key -- instead of the range
+ * partition.  Equal keys are contiguous and in input order, but groups are not
+ * in key order (the semisort_equal contract). */
+#define SS_FLAG_HASH_BUCKETS 0x4
 
 /* Bytes of workspace needed by `op` on n records with the given types and
  * options (NULL = defaults).  Returns SS_ERR_UNSUPPORTED for unsupported type

@@ -21,6 +21,8 @@ LIB_PATH = os.path.join(HERE, "_lib", "libsemisort.so")
 SS_U32, SS_U64, SS_U128 = 0, 1, 2
 OP_EQUAL, OP_LESS, OP_REDUCE, OP_HIST = 0, 1, 2, 3
 FLAG_PHASE_TIMING = 0x1
+FLAG_IDENTITY_HASH = 0x2
+FLAG_HASH_BUCKETS = 0x4
 
 STATUS = {
     0: "ok", 1: "invalid argument", 2: "unsupported type or size", 3: "workspace too small",

@@ -275,6 +275,10 @@ ss_status semisort_common(int op, ss_type kt, ss_type vt, const void* keys, cons
                           const ss_options* opt, ss_stream_t stream, const uint64_t* d_offsets = nullptr,
                           uint32_t num_inst = 0) {
   if (num_inst > 0 && !d_offsets) return SS_ERR_INVALID_ARG;
+  // semisort_< on hash buckets (SS_FLAG_HASH_BUCKETS): the semisort_= pipeline
+  // with a sorting base case
+  const bool hash_less = op == kOpLess && opt && (opt->flags & SS_FLAG_HASH_BUCKETS);
+  if (hash_less) op = kOpEqual;
   if (n == 0) return SS_OK;
   if (!keys || !keys_out || !ws) return SS_ERR_INVALID_ARG;
   if ((vals == nullptr) != (vals_out == nullptr)) return SS_ERR_INVALID_ARG;
@@ -313,6 +317,8 @@ ss_status semisort_common(int op, ss_type kt, ss_type vt, const void* keys, cons
   w.has_vals = vals != nullptr;
   w.splitter_mode = (op == kOpLess && opt && num_inst == 0) ? (uint32_t)opt->splitter_mode : 0u;
   w.offsets = d_offsets;
+  w.less_base = hash_less ? 1u : 0u;
+  w.ident = (opt && (opt->flags & SS_FLAG_IDENTITY_HASH) && kt != SS_U128) ? 1u : 0u;
   cudaStream_t st = reinterpret_cast<cudaStream_t>(stream);
   PhaseTimer* tm = timer_for(opt, st);
   cudaError_t e = dispatch(op, kt, vals ? (int)vt : 2, P, w, st, tm);
@@ -376,6 +382,7 @@ ss_status reduce_common(int op, ss_type kt, const void* keys, const uint64_t* va
   w.out_capacity = capacity;
   w.offsets = d_offsets;
   w.inst_off_out = d_out_offsets;
+  w.ident = (opt && (opt->flags & SS_FLAG_IDENTITY_HASH) && kt != SS_U128) ? 1u : 0u;
   PhaseTimer* tm = timer_for(opt, st);
   cudaError_t e = dispatch(op, kt, op == kOpReduce ? (int)SS_U64 : 2, P, w, st, tm);
   if (e == cudaErrorNotSupported) return SS_ERR_UNSUPPORTED;
@@ -395,6 +402,7 @@ ss_status ss_workspace_size(int op, ss_type key_type, ss_type val_type, uint64_t
                             size_t* bytes) {
   if (!bytes) return SS_ERR_INVALID_ARG;
   if (op < 0 || op > 3) return SS_ERR_INVALID_ARG;
+  if (op == SS_OP_SEMISORT_LESS && opt && (opt->flags & SS_FLAG_HASH_BUCKETS)) op = SS_OP_SEMISORT_EQUAL;
   Plan P;
   ss_status s = make_plan(op, key_type, val_type, n, opt, num_sms(), &P);
   if (s != SS_OK) return s;
@@ -434,6 +442,7 @@ ss_status histogram(ss_type key_type, const void* keys, void* ukeys_out, uint32_
 ss_status ss_workspace_size_batched(int op, ss_type key_type, ss_type val_type, uint64_t n, uint32_t num_instances,
                                     const ss_options* opt, size_t* bytes) {
   if (!bytes || op < 0 || op > 3 || num_instances == 0) return SS_ERR_INVALID_ARG;
+  if (op == SS_OP_SEMISORT_LESS && opt && (opt->flags & SS_FLAG_HASH_BUCKETS)) op = SS_OP_SEMISORT_EQUAL;
   Plan P;
   ss_status s = make_plan(op, key_type, val_type, n, opt, num_sms(), &P, num_instances);
   if (s != SS_OK) return s;

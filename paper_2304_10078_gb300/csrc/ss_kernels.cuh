@@ -74,9 +74,14 @@ __host__ __device__ __forceinline__ uint32_t hcap_of(uint32_t lbits) {
 // its open-addressing table (4 slots per heavy key, so probes stay short).
 template <class K>
 __device__ __forceinline__ uint32_t bucket_of(const K& k, uint64_t mult, uint32_t lbits, uint32_t nh,
-                                              const K* hk, const uint16_t* ht, uint32_t tmask) {
-  const uint64_t h = fold_key<K>(k) * mult;
-  uint32_t b = (uint32_t)(h >> (64 - lbits));
+                                              const K* hk, const uint16_t* ht, uint32_t tmask,
+                                              bool ident = false, uint32_t shift = 0) {
+  const uint64_t f = fold_key<K>(k);
+  const uint64_t h = f * mult;
+  // identity hashing (semisort-i, Sec. 4.1): the key's own bits, lowest first,
+  // each recursion level taking the next lbits bits
+  uint32_t b = ident ? (shift < 64 ? (uint32_t)(f >> shift) & ((1u << lbits) - 1) : 0u)
+                     : (uint32_t)(h >> (64 - lbits));
   if (nh) {
     uint32_t slot = (uint32_t)(h >> 20) & tmask;
     uint32_t e = ht[slot];
@@ -153,7 +158,7 @@ __device__ __forceinline__ uint32_t bucket_in(const K& k, const Seg& sg, const K
   if constexpr (OP == kOpLess)
     return bucket_less<K>(k, hk, ht, sg.nh);
   else
-    return bucket_of<K>(k, sg.mult, sg.lbits, sg.nh, hk, ht, tmask);
+    return bucket_of<K>(k, sg.mult, sg.lbits, sg.nh, hk, ht, tmask, sg.ident != 0, sg.shift);
 }
 
 // ----------------------------------------------------------------------------
@@ -193,6 +198,7 @@ static __global__ void __launch_bounds__(1024) k_init(Work w) {
       Seg s = {};
       s.start = 0;
       s.len = (uint32_t)w.n;
+      s.ident = w.ident;
       w.segs[0][0] = s;
       c->nsegs[0] = 1;
     }
@@ -231,6 +237,7 @@ static __global__ void __launch_bounds__(1024) k_init(Work w) {
       Seg s = {};
       s.start = off[i];
       s.len = (uint32_t)len;
+      s.ident = w.ident;
       w.segs[0][carry[1] + eb] = s;
     }
     __syncthreads();
@@ -1259,6 +1266,8 @@ __global__ void __launch_bounds__(1024) k_emit(Work w, LevelBufs lb) {
           Seg ns2 = {};
           ns2.start = start;
           ns2.len = sz;
+          ns2.shift = sg.shift + sg.lbits;
+          ns2.ident = sg.ident;
           w.segs[lb.level + 1][j] = ns2;
         }
       }

@@ -91,6 +91,7 @@ cudaError_t launch_pipeline(const Plan& P, const Work& w, cudaStream_t st, const
   if constexpr (OP == kOpEqual) {
     ref_smem = sizeof(RefSmem<K, V>);
     if ((e = set_smem(k_finish_equal<K, V>, ref_smem)) != cudaSuccess) return e;
+    if ((e = set_smem(k_finish_less<K, V>, sizeof(LessSmem<K, V>))) != cudaSuccess) return e;
   } else if constexpr (OP == kOpLess) {
     ref_smem = sizeof(LessSmem<K, V>);
     if ((e = set_smem(k_finish_less<K, V>, ref_smem)) != cudaSuccess) return e;
@@ -158,7 +159,10 @@ cudaError_t launch_pipeline(const Plan& P, const Work& w, cudaStream_t st, const
     }
   }
   if constexpr (OP == kOpEqual) {
-    k_finish_equal<K, V><<<nsm * 2, kRT, ref_smem, st>>>(w);
+    if (w.less_base)  // hash buckets with a sorting base case: the paper's semisort_<
+      k_finish_less<K, V><<<nsm * 2, kRT, sizeof(LessSmem<K, V>), st>>>(w);
+    else
+      k_finish_equal<K, V><<<nsm * 2, kRT, ref_smem, st>>>(w);
     ++nl;
     if (tm) tm->mark("refine");
   } else if constexpr (OP == kOpLess) {

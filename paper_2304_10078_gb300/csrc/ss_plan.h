@@ -65,6 +65,8 @@ struct Seg {
   uint32_t cnt_next;   // next-level segments emitted
   uint32_t nb;         // bucket ids in use
   uint64_t mult;       // odd multiplier of this segment's bucketing hash
+  uint32_t shift;      // identity hashing: first key bit of this segment's light-bucket id
+  uint32_t ident;      // bucket ids from the key's own bits (identity hash)
 };
 
 struct Tile {
@@ -103,7 +105,8 @@ struct Work {
   uint32_t lbits1;     // log2 n_L at level 1
   uint32_t s1, s2;     // sample size caps at level 1 / levels >= 2
   uint32_t op;
-  uint32_t ident;      // identity hash for integer keys
+  uint32_t ident;      // identity hash for integer keys (bucket ids from the key's own bits)
+  uint32_t less_base;  // semisort_< with hash buckets: sort each base case
   uint32_t out_cap;    // collect-reduce / histogram capacity (clamped)
   uint64_t seed;
   // user buffers
