@@ -25,7 +25,7 @@
  *    run concurrently.
  *  - Return values report argument errors found on the host at enqueue time.
  *    Failures found on the device (an internal capacity limit, the recursion
- *    depth limit) set a flag in the workspace; ss_last_device_error() reads
+ *    depth limit of six levels) set a flag in the workspace; ss_last_device_error() reads
  *    and clears it.  Each call resets the flag when it starts, so the flag
  *    describes the most recent call on that workspace.  No kernel traps.
  *  - n = 0 is valid and enqueues nothing.  n must be below 2^32 - 2^20.
@@ -246,7 +246,7 @@ ss_status ss_last_device_error(void* ws, ss_stream_t stream, int* code);
 
 /* Per-call statistics kept in the workspace by the last call (synchronizes the
  * stream).  out[0..count) receives, in order: levels used, records distributed
- * at levels 1..4 (4 entries), records refined, records copied, heavy keys at
+ * at levels 1, 2, 3 and 4-6 (4 entries), records refined, records copied, heavy keys at
  * level 1, largest refined bucket, refine items, records whose bucket was all
  * distinct keys, splitters of the semisort_< top level (0 sampled, 1 learned,
  * 2 learned but rejected on the sample), the largest top-level range bucket's

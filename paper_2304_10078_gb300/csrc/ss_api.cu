@@ -177,9 +177,9 @@ ss_status make_plan(int op, int kt, int vt, uint64_t n, const ss_options* opt, i
   P->off_toptab = o;
   o = al(o + (wide && multi ? sizeof(TopTable) : 0));
   P->off_inst_base = o;
-  o = al(o + (batched && red ? (size_t)5 * num_inst * 8 : 0));
+  o = al(o + (batched && red ? (size_t)kItemClasses * num_inst * 8 : 0));
   P->off_inst_first = o;
-  o = al(o + (batched && red ? (size_t)5 * num_inst * 8 : 0));
+  o = al(o + (batched && red ? (size_t)kItemClasses * num_inst * 8 : 0));
   P->off_ctrl = 0;
   P->total = o;
   return SS_OK;

@@ -322,7 +322,8 @@ __global__ void __launch_bounds__(1024) k_plan(Work w, int level) {
         tl.pad = 0;
         tiles[sg.first_tile + t] = tl;
       }
-      atomicAdd((unsigned long long*)&w.ctrl->stats[1 + level], (unsigned long long)sg.len);
+      // records distributed per level (levels 4 and deeper share the last entry)
+      atomicAdd((unsigned long long*)&w.ctrl->stats[1 + (level < 3 ? level : 3)], (unsigned long long)sg.len);
     }
     __syncthreads();
     if (threadIdx.x == 0) {
@@ -1573,8 +1574,23 @@ __global__ void __launch_bounds__(kRT, 2) k_finish_less(Work w) {
           for (int r = 0; r < kRR; ++r) g[r] = sm.px[bpad(c0t + r)];
         }
       }
-      // finish every run of equal buckets by a stable insertion sort on the key
+      // finish every run of equal buckets by a stable insertion sort on the key.
+      // With shift 0 a bucket holds one key value: the rank is already the sort.
+      // Otherwise look for an out-of-order neighbour first (in parallel).
       auto key_at = [&](uint32_t x) { return sm.S[sw<RB>(x & 0xFFFFu)].k; };
+      bool any = false;
+      if (shift > 0) {
+        for (uint32_t p = 1 + tid; p < m; p += kRT) {
+          const uint32_t x = sm.px[bpad(p)], y = sm.px[bpad(p - 1)];
+          if ((x >> 16) == (y >> 16) && KeyT<K>::lt(key_at(x), key_at(y))) any = true;
+        }
+      }
+      if (!__syncthreads_or(any)) {
+        for (uint32_t p = tid; p < m; p += kRT)
+          store_out<K, V>(w, it.start + p, sm.S[sw<RB>(sm.px[bpad(p)] & 0xFFFFu)]);
+        __syncthreads();
+        continue;
+      }
       for (uint32_t p = tid; p < m; p += kRT) {
         const uint32_t b = sm.px[bpad(p)] >> 16;
         if (p > 0 && (sm.px[bpad(p - 1)] >> 16) == b) continue;  // not a run start
@@ -1883,7 +1899,7 @@ __device__ __forceinline__ uint32_t instance_of(const Work& w, uint64_t start) {
 }
 
 static __global__ void k_inst_reset(Work w) {
-  const uint32_t m = 5 * w.num_inst;
+  const uint32_t m = kItemClasses * w.num_inst;
   for (uint32_t i = blockIdx.x * blockDim.x + threadIdx.x; i < m; i += gridDim.x * blockDim.x) {
     w.inst_base[i] = 0;
     w.inst_first[i] = ~0ull;
@@ -1908,9 +1924,9 @@ static __global__ void __launch_bounds__(1024) k_inst_scan(Work w) {
   __syncthreads();
   for (uint32_t i0 = 0; i0 < ni; i0 += blockDim.x) {
     const uint32_t i = i0 + threadIdx.x;
-    uint64_t u[5], tot = 0;
+    uint64_t u[kItemClasses], tot = 0;
 #pragma unroll
-    for (int c = 0; c < 5; ++c) {
+    for (uint32_t c = 0; c < kItemClasses; ++c) {
       u[c] = i < ni ? w.inst_base[(uint64_t)c * ni + i] : 0;
       tot += u[c];
     }
@@ -1921,7 +1937,7 @@ static __global__ void __launch_bounds__(1024) k_inst_scan(Work w) {
       w.inst_off_out[i] = ex;
       uint64_t b = ex;
 #pragma unroll
-      for (int c = 0; c < 5; ++c) {
+      for (uint32_t c = 0; c < kItemClasses; ++c) {
         w.inst_base[(uint64_t)c * ni + i] = b;
         b += u[c];
       }

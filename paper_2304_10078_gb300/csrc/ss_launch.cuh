@@ -177,7 +177,7 @@ cudaError_t launch_pipeline(const Plan& P, const Work& w, cudaStream_t st, const
     k_iscan_b<<<1, 1024, 0, st>>>(w);
     k_iscan_c<<<nch, 1024, 0, st>>>(w);
     if (w.offsets) {  // batched: make each instance's outputs contiguous
-      const uint32_t g = (5 * w.num_inst + 255) / 256;
+      const uint32_t g = (kItemClasses * w.num_inst + 255) / 256;
       k_inst_reset<<<g < 1024 ? g : 1024, 256, 0, st>>>(w);
       k_inst_accum<<<nsm * 4, 256, 0, st>>>(w);
       k_inst_scan<<<1, 1024, 0, st>>>(w);

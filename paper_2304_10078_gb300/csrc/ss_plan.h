@@ -11,7 +11,7 @@
 
 namespace ss {
 
-constexpr int kMaxLevels = 4;          // recursion levels (Algorithm 1) before the depth error
+constexpr int kMaxLevels = 6;          // recursion levels (Algorithm 1) before the depth error
 constexpr int kMaxLightLog2 = 9;       // n_L <= 512 per segment
 constexpr uint32_t kMaxHeavy = 512;    // heavy keys per segment
 constexpr uint32_t kMaxBuckets = 1024; // n_L + heavy: bucket ids fit two 5-bit rank passes
@@ -45,6 +45,9 @@ struct TopTable {
 // Finish items of a batched call's instances of at most alpha records carry
 // this level tag (they go straight to the base case).
 constexpr uint32_t kDirectLevel = kMaxLevels;
+// Item classes of a batched call's output placement: direct items, then one
+// per distribution level.
+constexpr uint32_t kItemClasses = kMaxLevels + 1;
 
 // Finish-item kinds.
 enum ItemKind : uint32_t { kItemRefine = 0, kItemCopy = 1, kItemHeavyOut = 2 };
@@ -148,7 +151,7 @@ struct Work {
   // batched calls: instance i holds records [offsets[i], offsets[i+1])
   const uint64_t* offsets;  // device, num_inst + 1 entries; null for a single instance
   uint32_t num_inst;
-  uint64_t* inst_base;      // collect-reduce / histogram: per (class, instance) output base (5 x num_inst)
+  uint64_t* inst_base;      // collect-reduce / histogram: per (class, instance) output base (kItemClasses x num_inst)
   uint64_t* inst_first;     // per (class, instance) first item position in the item scan
   uint64_t* inst_off_out;   // user: num_inst + 1 output offsets
   uint32_t* scratch32;  // histogram: per-position counts of compacted base cases

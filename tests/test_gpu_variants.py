@@ -104,3 +104,26 @@ def test_hash_bucket_semisort_less(ss, kind, n):
     assert oracle.check_semisort_equal(keys, vals, ko, vo) is None
     if n <= 4096:  # a single base case: fully sorted
         assert np.array_equal(ko, oracle.stable_sort(keys)[0])
+
+
+@pytest.mark.parametrize("op", ["equal", "less_hash"])
+def test_hash_buckets_keys_with_many_copies(ss, op):
+    """floor(Exp(lambda)) with about a thousand copies per key value: such keys
+    stay light at shallow levels and must be separated deeper down without
+    reaching the recursion-depth limit."""
+    import torch
+    n = 1 << 24
+    keys = synth.exponential(96, n, 6e-5)
+    vals = np.arange(n, dtype=np.uint64)
+    k, v = to_dev(keys), to_dev(vals)
+    if op == "equal":
+        o = ss.make_options(seed=1)
+        ws = ss.alloc_workspace(ss.OP_EQUAL, k, v, o)
+        ko, vo = ss.semisort_equal(k, v, workspace=ws, options=o)
+    else:
+        o = ss.make_options(seed=1, flags=ss.FLAG_HASH_BUCKETS)
+        ws = ss.alloc_workspace(ss.OP_LESS, k, v, o)
+        ko, vo = ss.semisort_less(k, v, workspace=ws, options=o)
+    torch.cuda.synchronize()
+    assert ss.last_device_error(ws) == 0
+    assert oracle.check_semisort_equal(keys, vals, to_host(ko), to_host(vo)) is None
