@@ -318,6 +318,7 @@ ss_status semisort_common(int op, ss_type kt, ss_type vt, const void* keys, cons
   w.splitter_mode = (op == kOpLess && opt && num_inst == 0) ? (uint32_t)opt->splitter_mode : 0u;
   w.offsets = d_offsets;
   w.less_base = hash_less ? 1u : 0u;
+  w.auto_nl = (opt && opt->n_light_log2) ? 0u : 1u;
   w.ident = (opt && (opt->flags & SS_FLAG_IDENTITY_HASH) && kt != SS_U128) ? 1u : 0u;
   cudaStream_t st = reinterpret_cast<cudaStream_t>(stream);
   PhaseTimer* tm = timer_for(opt, st);
@@ -382,6 +383,7 @@ ss_status reduce_common(int op, ss_type kt, const void* keys, const uint64_t* va
   w.out_capacity = capacity;
   w.offsets = d_offsets;
   w.inst_off_out = d_out_offsets;
+  w.auto_nl = (opt && opt->n_light_log2) ? 0u : 1u;
   w.ident = (opt && (opt->flags & SS_FLAG_IDENTITY_HASH) && kt != SS_U128) ? 1u : 0u;
   PhaseTimer* tm = timer_for(opt, st);
   cudaError_t e = dispatch(op, kt, op == kOpReduce ? (int)SS_U64 : 2, P, w, st, tm);

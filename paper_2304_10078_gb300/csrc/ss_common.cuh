@@ -261,13 +261,15 @@ struct alignas(sizeof(K) >= 16 ? 16 : sizeof(K)) RecT<K, void> {
 // XOR swizzle inside every 128-byte row keeps both access patterns of the
 // kernels free of bank conflicts: consecutive i (coalesced copies) and
 // i = 16 t + r for t = 0..31 (thread t holding 16 consecutive records).
-template <int RB>
+// PER = records each thread holds in the blocked pattern (a power of two).
+template <int RB, int PER = 16>
 __device__ __forceinline__ uint32_t sw(uint32_t i) {
   constexpr uint32_t L = RB >= 128 ? 1u : 128u / RB;  // records per 128-byte row
+  constexpr int SH = PER == 16 ? 4 : PER == 8 ? 3 : PER == 4 ? 2 : 4;
   if constexpr (L <= 1)
     return i;
   else
-    return (i & ~(L - 1)) | ((i ^ (i >> 4)) & (L - 1));
+    return (i & ~(L - 1)) | ((i ^ (i >> SH)) & (L - 1));
 }
 
 template <class V>

@@ -68,26 +68,34 @@ __host__ __device__ __forceinline__ uint32_t hcap_of(uint32_t lbits) {
   return nl < kMaxHeavy ? nl : kMaxHeavy;
 }
 
+// Heavy-key capacity of a segment (a power of two): hash-bucket segments keep
+// n_L + capacity <= kMaxBuckets, range segments use hcap_of.
+template <int OP>
+__device__ __forceinline__ uint32_t seg_hcap(const Seg& sg) {
+  return OP == kOpLess ? hcap_of(sg.lbits) : sg.nbcap - sg.nl;
+}
+
 // Bucket of key k in its segment (GetBucketId of Algorithm 1): the heavy
 // bucket n_L + i if k is the i-th heavy key, else the light bucket given by
 // the top lbits bits of the level hash.  hk/ht: the segment's heavy keys and
 // its open-addressing table (4 slots per heavy key, so probes stay short).
+// The light bucket is the hash scaled to [0, n_L): the top bits of the
+// product when n_L is a power of two.
 template <class K>
-__device__ __forceinline__ uint32_t bucket_of(const K& k, uint64_t mult, uint32_t lbits, uint32_t nh,
+__device__ __forceinline__ uint32_t bucket_of(const K& k, uint64_t mult, uint32_t nl, uint32_t nh,
                                               const K* hk, const uint16_t* ht, uint32_t tmask,
                                               bool ident = false, uint32_t shift = 0) {
   const uint64_t f = fold_key<K>(k);
   const uint64_t h = f * mult;
   // identity hashing (semisort-i, Sec. 4.1): the key's own bits, lowest first,
-  // each recursion level taking the next lbits bits
-  uint32_t b = ident ? (shift < 64 ? (uint32_t)(f >> shift) & ((1u << lbits) - 1) : 0u)
-                     : (uint32_t)(h >> (64 - lbits));
+  // each recursion level taking the next log2(n_L) bits (n_L a power of two)
+  uint32_t b = ident ? (shift < 64 ? (uint32_t)(f >> shift) & (nl - 1) : 0u) : (uint32_t)__umul64hi(h, nl);
   if (nh) {
     uint32_t slot = (uint32_t)(h >> 20) & tmask;
     uint32_t e = ht[slot];
     while (e != 0xFFFFu) {
       if (KeyT<K>::eq(hk[e], k)) {
-        b = (1u << lbits) + e;
+        b = nl + e;
         break;
       }
       slot = (slot + 1) & tmask;
@@ -158,7 +166,7 @@ __device__ __forceinline__ uint32_t bucket_in(const K& k, const Seg& sg, const K
   if constexpr (OP == kOpLess)
     return bucket_less<K>(k, hk, ht, sg.nh);
   else
-    return bucket_of<K>(k, sg.mult, sg.lbits, sg.nh, hk, ht, tmask, sg.ident != 0, sg.shift);
+    return bucket_of<K>(k, sg.mult, sg.nl, sg.nh, hk, ht, tmask, sg.ident != 0, sg.shift);
 }
 
 // ----------------------------------------------------------------------------
@@ -284,10 +292,20 @@ __global__ void __launch_bounds__(1024) k_plan(Work w, int level) {
         lb = lb > (uint32_t)kMaxLightLog2 ? (uint32_t)kMaxLightLog2 : lb;
       }
       if (OP == kOpLess && !top_single && lb > kMaxLightLog2 - 1) lb = kMaxLightLog2 - 1;
-      const uint32_t nl = 1u << lb;
+      uint32_t nl = 1u << lb, hcap = hcap_of(lb);
+      // hash buckets: a segment wanting more than 512 light buckets gets 768
+      // (and room for 256 heavy keys), still 1024 bucket ids in all
+      if (OP != kOpLess && !sg.ident && lb == (uint32_t)kMaxLightLog2 && (!top_single || w.auto_nl)) {
+        const uint64_t want = (2ull * (top_single ? w.n : sg.len) + w.alpha - 1) / w.alpha;
+        if (want > 512) {
+          nl = 768;
+          hcap = 256;
+        }
+      }
       sg.lbits = lb;
+      sg.nl = nl;
       // semisort_<: q <= (n_L - 1) + n_L boundaries give 2q + 1 < 4 n_L bucket ids
-      sg.nbcap = OP == kOpLess ? 4 * nl : nl + hcap_of(lb);
+      sg.nbcap = OP == kOpLess ? 4 * nl : nl + hcap;
       sg.nh = 0;
       sg.nb = nl;
       sg.mult = seg_mult(w.seed, level, sg.start);
@@ -361,7 +379,7 @@ __global__ void __launch_bounds__(1024) k_sample(Work w, LevelBufs lb, uint32_t 
   for (uint32_t s = blockIdx.x; s < ns; s += gridDim.x) {
     const Seg sg = w.segs[lb.level][s];
     if (sg.lbits == 0) continue;
-    const uint32_t hcap = hcap_of(sg.lbits);
+    const uint32_t hcap = seg_hcap<OP>(sg);
     uint32_t S_n = 16u * hcap;
     if (S_n > s_cap) S_n = s_cap;
     const uint32_t tau = S_n / hcap;
@@ -420,7 +438,7 @@ __global__ void __launch_bounds__(1024) k_sample(Work w, LevelBufs lb, uint32_t 
     if constexpr (OP == kOpLess) {
       if (threadIdx.x == 0) {
         // merge splitters S[j S_n / n_L] (deduplicated) with the heavy keys
-        const uint32_t nl = 1u << sg.lbits;
+        const uint32_t nl = sg.nl;
         K* bnd = reinterpret_cast<K*>(w.splitters[lb.level]) + sg.bbase;
         uint32_t q = 0, j = 1, hi = 0;
         bool have_last = false;
@@ -460,7 +478,7 @@ __global__ void __launch_bounds__(1024) k_sample(Work w, LevelBufs lb, uint32_t 
       for (uint32_t t = threadIdx.x; t < tsize; t += blockDim.x) ht[t] = (uint16_t)(tab[t] == kEmpty ? 0xFFFFu : tab[t]);
       if (threadIdx.x == 0) {
         w.segs[lb.level][s].nh = nh;
-        w.segs[lb.level][s].nb = (1u << sg.lbits) + nh;
+        w.segs[lb.level][s].nb = sg.nl + nh;
         if (lb.level == 0) w.ctrl->stats[7] = nh;
       }
     }
@@ -715,7 +733,7 @@ __device__ __forceinline__ void load_heavy(const Work& w, int level, const Seg& 
       ht[i] = gf[i];
     }
   } else if (sg.nh) {
-    const uint32_t tsize = 4 * hcap_of(sg.lbits);
+    const uint32_t tsize = 4 * seg_hcap<OP>(sg);
     const K* ghk = reinterpret_cast<const K*>(w.hkeys[level]) + sg.bbase;
     const uint16_t* ght = w.htab[level] + 2ull * sg.bbase;
     for (uint32_t i = threadIdx.x; i < sg.nh; i += blockDim.x) hk[i] = ghk[i];
@@ -773,9 +791,9 @@ __global__ void __launch_bounds__(kCountThreads) k_count(Work w, LevelBufs lb) {
   for (uint32_t t = blockIdx.x; t < nt; t += gridDim.x) {
     const Tile tl = w.tiles[lb.level][t];
     const Seg sg = w.segs[lb.level][tl.seg];
-    const uint32_t nl = 1u << sg.lbits;
+    const uint32_t nl = sg.nl;
     const uint32_t nb = sg.nb;
-    const uint32_t tmask = 4 * hcap_of(sg.lbits) - 1;
+    const uint32_t tmask = 4 * seg_hcap<OP>(sg) - 1;
     load_heavy<K, OP>(w, lb.level, sg, hk, ht);
     uint64_t tkmin = 0;
     uint32_t tshift = 0;
@@ -933,7 +951,7 @@ __global__ void __launch_bounds__(1024) k_scan(Work w, LevelBufs lb) {
       }
       continue;
     }
-    const uint32_t nl = 1u << sg.lbits;
+    const uint32_t nl = sg.nl;
     const uint32_t nb = sg.nb;
     uint32_t* C = w.C[lb.level] + sg.cbase;
     uint32_t* bsize = w.bsize[lb.level] + sg.bbase;
@@ -1033,7 +1051,7 @@ __device__ __forceinline__ RecT<K, V> read_src(const LevelBufs& lb, uint64_t i) 
 
 // Coalesced copy of `len` records starting at global index g into S; eight
 // independent loads per thread are in flight before the first store.
-template <int NT, class K, class V, class Src>
+template <int NT, class K, class V, class Src, int PER = 16>
 __device__ __forceinline__ void load_chunk(RecT<K, V>* S, uint32_t len, Src src) {
   using Rec = RecT<K, V>;
   constexpr int B = 8;
@@ -1047,7 +1065,7 @@ __device__ __forceinline__ void load_chunk(RecT<K, V>* S, uint32_t len, Src src)
 #pragma unroll
     for (int u = 0; u < B; ++u) {
       const uint32_t i = i0 + u * NT + threadIdx.x;
-      if (i < len) S[sw<sizeof(Rec)>(i)] = t[u];
+      if (i < len) S[sw<sizeof(Rec), PER>(i)] = t[u];
     }
   }
 }
@@ -1068,9 +1086,9 @@ __global__ void __launch_bounds__(kDT, 2) k_distribute(Work w, LevelBufs lb) {
   for (uint32_t t = blockIdx.x; t < nt; t += gridDim.x) {
     const Tile tl = w.tiles[lb.level][t];
     const Seg sg = w.segs[lb.level][tl.seg];
-    const uint32_t nl = 1u << sg.lbits;
+    const uint32_t nl = sg.nl;
     const uint32_t nb = sg.nb;
-    const uint32_t tmask = 4 * hcap_of(sg.lbits) - 1;
+    const uint32_t tmask = 4 * seg_hcap<OP>(sg) - 1;
     load_heavy<K, OP>(w, lb.level, sg, sm.hk, sm.ht);
     uint64_t tkmin = 0;
     uint32_t tshift = 0;
@@ -1207,7 +1225,7 @@ __global__ void __launch_bounds__(1024) k_emit(Work w, LevelBufs lb) {
   for (uint32_t s = blockIdx.x; s < ns; s += gridDim.x) {
     const Seg sg = w.segs[lb.level][s];
     if (sg.lbits == 0) continue;
-    const uint32_t nl = 1u << sg.lbits;
+    const uint32_t nl = sg.nl;
     const uint32_t nb = sg.nb;
     const uint32_t* bsize = w.bsize[lb.level] + sg.bbase;
     const uint32_t* boff = w.boff[lb.level] + sg.bbase;
@@ -1386,8 +1404,9 @@ __global__ void __launch_bounds__(kRT, 2) k_finish_equal(Work w) {
       uint32_t s = 0;
       if (c < m) {
         const K key = sm.S[sw<RB>(c)].k;
-        const uint64_t h = KeyT<K>::hash(key, salt, false);
-        s = (uint32_t)h & (ts - 1);
+        // multiply-shift with the refine salt (bits independent of the bucketing)
+        const uint64_t h = fold_key<K>(key) * (salt | 1);
+        s = (uint32_t)(h >> 40) & (ts - 1);
         while (true) {
           uint32_t e = sm.u.table[s];
           if (e == kEmpty) {

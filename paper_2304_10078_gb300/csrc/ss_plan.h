@@ -70,6 +70,8 @@ struct Seg {
   uint64_t mult;       // odd multiplier of this segment's bucketing hash
   uint32_t shift;      // identity hashing: first key bit of this segment's light-bucket id
   uint32_t ident;      // bucket ids from the key's own bits (identity hash)
+  uint32_t nl;         // light buckets n_L (a power of two, or 768)
+  uint32_t pad;
 };
 
 struct Tile {
@@ -110,6 +112,7 @@ struct Work {
   uint32_t op;
   uint32_t ident;      // identity hash for integer keys (bucket ids from the key's own bits)
   uint32_t less_base;  // semisort_< with hash buckets: sort each base case
+  uint32_t auto_nl;    // top-level n_L chosen by size (no n_light_log2 option)
   uint32_t out_cap;    // collect-reduce / histogram capacity (clamped)
   uint64_t seed;
   // user buffers
