@@ -122,10 +122,22 @@ def cpu_oracle_sample(sample_n: int, dists) -> dict:
                       f"(same generators and seed as the GPU workload); std::stable_sort, 1 thread"}
 
 
+def headline_config(n, dists, world):
+    return {"workload": f"semisort_equal n={n} (u64 key, u64 value=index), steps cycle over "
+                        + ", ".join(dist_name(d) for d in dists),
+            "parallelism": "replicas" if world > 1 else "single GPU",
+            "l2": f"inputs ({16 * n / 1e9:.3g} GB per step) larger than L2; no flush"}
+
+
 def run_reference(args, rank, world):
+    """The reference arm: the oracle (the stable sort that defines a valid
+    semisort_= output) on the host cores, each step a bounded sample -- the
+    first ref_sample records -- of the step's distribution of the headline
+    workload (same generators and seed), cycling over the same ten
+    distributions."""
     if rank != 0:
         return 0
-    dists = DISTS[5:10:2] if args.quick else [DISTS[3], DISTS[8]]
+    dists = [DISTS[int(i)] for i in args.dists.split(",")] if args.dists else DISTS
     sample_n = args.ref_sample
     t_steps = []
     for i in range(args.warmup + args.steps):
@@ -137,10 +149,10 @@ def run_reference(args, rank, world):
     line = {"impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world,
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1000 * total_t / args.steps,
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "u64", "data": "synthetic",
-            "config": {"workload": f"semisort_equal oracle (std::stable_sort) on {sample_n}-record samples of "
-                                   f"{', '.join(dist_name(d) for d in dists)}"},
+            "config": headline_config(args.n, dists, world),
             "cpu_baseline": {"value": value, "unit": UNIT, "cores": 1, "kind": "oracle",
-                             "sample": f"{sample_n} records per step"},
+                             "sample": f"first {sample_n} records of each step's distribution; std::stable_sort, "
+                                       f"1 thread"},
             "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
     print(json.dumps(line))
     return 0
@@ -588,10 +600,7 @@ def main():
         "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": ms_step, "higher_is_better": True, "scaling": "weak",
         "vs_baseline": None, "dtype": "u64", "data": "synthetic",
-        "config": {"workload": f"semisort_equal n={n} (u64 key, u64 value=index), steps cycle over "
-                               + ", ".join(dist_name(d) for d in dists),
-                   "parallelism": "replicas" if world > 1 else "single GPU",
-                   "l2": f"inputs ({16 * n / 1e9:.3g} GB per step) larger than L2; no flush"},
+        "config": headline_config(n, dists, world),
         "roofline": {"bound": "hbm", "kernel": "distribute.L0",
                      "achieved": achieved, "peak": peak, "peak_kind": peak_kind, "unit": "GB/s",
                      "frac": (achieved / peak) if achieved else None, "traffic": traffic,
