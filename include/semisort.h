@@ -147,8 +147,9 @@ ss_status histogram(ss_type key_type, const void* keys, void* ukeys_out, uint32_
  * shared by every call on a device; it keeps whatever the last call left in it.
  * Limits and behaviour:
  *  - n <= 262144 (2^18) records; larger n returns SS_ERR_UNSUPPORTED.  Options
- *    whose plan would not fit the array (ss_workspace_size() above 24 MiB)
- *    return SS_ERR_WORKSPACE_TOO_SMALL.
+ *    whose plan would not fit the array (ss_workspace_size() above 24 MiB, which
+ *    only 128-bit keys with alpha below 256 reach) return
+ *    SS_ERR_WORKSPACE_TOO_SMALL.
  *  - The first call on each device looks up the array's device address
  *    (cudaGetSymbolAddress) and remembers it; make that first call before any
  *    stream capture begins.

@@ -561,7 +561,7 @@ ss_status ss_hash_u64(const uint64_t* keys, uint64_t* out, uint64_t n, uint64_t 
 namespace {
 
 constexpr uint64_t kNoAllocMaxN = 1ull << 18;      // records per call
-constexpr size_t kNoAllocBytes = 24ull << 20;      // covers every plan up to kNoAllocMaxN with alpha >= 64
+constexpr size_t kNoAllocBytes = 24ull << 20;      // every plan of kNoAllocMaxN u32/u64 keys; 128-bit keys need alpha >= 256
 
 static __device__ __align__(256) unsigned char g_noalloc_ws[kNoAllocBytes];
 
