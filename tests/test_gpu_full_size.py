@@ -1,0 +1,111 @@
+"""Parity at the full size of the benchmark (n = 10^9, u64 key, u64 value =
+index, default options as bench.py times them), through properties that hold
+at any size and that the GPU can check in full:
+
+* semisort_= / semisort_<: the values form a permutation of 0..n-1, every
+  output record is an input record (key = input key of its value), records of
+  equal keys keep input order (values increase along each run), equal keys
+  are contiguous (runs = distinct keys); semisort_< keys do not decrease.
+* collect-reduce: the unique count is the number of distinct keys, the keys
+  are distinct, and the sums add up to n(n-1)/2 mod 2^64 (value = index).
+* histogram: the unique count is the number of distinct keys and the counts
+  add up to n.
+"""
+import pytest
+
+pytestmark = pytest.mark.gpu
+
+N = 10**9
+SEED = 0x5EED0002
+
+
+@pytest.fixture(scope="module")
+def env():
+    import torch
+    if not torch.cuda.is_available():
+        pytest.skip("no GPU")
+    if torch.cuda.get_device_properties(0).total_memory < 200 * 2**30:
+        pytest.skip("needs a GPU with about 200 GB")
+    import paper_2304_10078_gb300 as ss
+    import synth.gpu as sg
+    ss.build()
+    vals = sg.iota(N)
+    return ss, sg, vals
+
+
+def keys_of(sg, kind, p):
+    return sg.uniform_exact(SEED, N, p) if kind == "uniform" else sg.zipf(SEED, N, p)
+
+
+def distinct(torch, k):
+    s, _ = torch.sort(k.view(torch.int64))
+    return int((s[1:] != s[:-1]).sum().item()) + 1
+
+
+def check_semisort(torch, keys, vals_out, keys_out, ordered):
+    ki, ko, vo = keys.view(torch.int64), keys_out.view(torch.int64), vals_out.view(torch.int64)
+    seen = torch.zeros(N, dtype=torch.bool, device="cuda")
+    seen[vo] = True
+    assert bool(seen.all()), "values are not a permutation"
+    del seen
+    assert bool((ki[vo] == ko).all()), "a record's key changed"
+    same = ko[1:] == ko[:-1]
+    assert bool((vo[1:][same] > vo[:-1][same]).all()), "equal keys out of input order"
+    runs = int((~same).sum().item()) + 1
+    assert runs == distinct(torch, ki), "equal keys not contiguous"
+    if ordered:
+        flip = ko ^ (-(2**63))  # unsigned order as signed order
+        assert bool((flip[1:] >= flip[:-1]).all()), "keys decrease"
+
+
+@pytest.mark.parametrize("kind,p", [("uniform", 10**7), ("zipf", 0.8), ("uniform", 10**9)])
+def test_semisort_equal_full_size(env, kind, p):
+    import torch
+    ss, sg, vals = env
+    keys = keys_of(sg, kind, p)
+    o = ss.make_options(seed=1)
+    ws = ss.alloc_workspace(ss.OP_EQUAL, keys, vals, o)
+    ko, vo = ss.semisort_equal(keys, vals, workspace=ws, options=o)
+    torch.cuda.synchronize()
+    assert ss.last_device_error(ws) == 0
+    del ws
+    check_semisort(torch, keys, vo, ko, ordered=False)
+
+
+@pytest.mark.parametrize("kind,p", [("uniform", 10**9), ("zipf", 1.2)])
+def test_semisort_less_full_size(env, kind, p):
+    import torch
+    ss, sg, vals = env
+    keys = keys_of(sg, kind, p)
+    o = ss.make_options(seed=1)
+    ws = ss.alloc_workspace(ss.OP_LESS, keys, vals, o)
+    ko, vo = ss.semisort_less(keys, vals, workspace=ws, options=o)
+    torch.cuda.synchronize()
+    assert ss.last_device_error(ws) == 0
+    del ws
+    check_semisort(torch, keys, vo, ko, ordered=True)
+
+
+def test_collect_reduce_and_histogram_full_size(env):
+    import torch
+    ss, sg, vals = env
+    keys = keys_of(sg, "zipf", 1.2)
+    d = distinct(torch, keys)
+    o = ss.make_options(seed=1)
+    ws = ss.alloc_workspace(ss.OP_REDUCE, keys, vals, o)
+    uk, sums, nu = ss.collect_reduce(keys, vals, workspace=ws, options=o)
+    torch.cuda.synchronize()
+    assert ss.last_device_error(ws) == 0
+    u = int(nu.view(torch.int64)[0].item())
+    assert u == d
+    assert distinct(torch, uk[:u]) == u
+    total = int(sums[:u].view(torch.int64).sum().item()) % 2**64  # int64 sums wrap like u64
+    assert total == (N * (N - 1) // 2) % 2**64
+    del uk, sums, ws
+    ws = ss.alloc_workspace(ss.OP_HIST, keys, None, o)
+    hk, cnt, nh = ss.histogram(keys, workspace=ws, options=o)
+    torch.cuda.synchronize()
+    assert ss.last_device_error(ws) == 0
+    h = int(nh.view(torch.int64)[0].item())
+    assert h == d
+    assert int(cnt[:h].view(torch.int32).to(torch.int64).sum().item()) == N
