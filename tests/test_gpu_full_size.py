@@ -109,3 +109,53 @@ def test_collect_reduce_and_histogram_full_size(env):
     h = int(nh.view(torch.int64)[0].item())
     assert h == d
     assert int(cnt[:h].view(torch.int32).to(torch.int64).sum().item()) == N
+
+
+def test_semisort_less_learned_full_size(env):
+    import torch
+    ss, sg, vals = env
+    keys = keys_of(sg, "uniform", 10**9)
+    o = ss.make_options(seed=1, splitter_mode=1)
+    ws = ss.alloc_workspace(ss.OP_LESS, keys, vals, o)
+    ko, vo = ss.semisort_less(keys, vals, workspace=ws, options=o)
+    torch.cuda.synchronize()
+    assert ss.last_device_error(ws) == 0
+    assert ss.stats(ws)["l0_splitters"] == 1  # the trained model was used
+    del ws
+    check_semisort(torch, keys, vo, ko, ordered=True)
+
+
+def test_batched_semisort_equal_full_size(env):
+    """The 4096-instance workload of the benchmark (about 1.7 * 10^9 records):
+    every output value stays inside its own instance's range, records are
+    intact and stable, and the runs add up to the distinct keys of every
+    instance."""
+    import torch
+
+    import bench
+    ss, sg, _ = env
+    off_h, keys, n = bench.batched_workload(sg, torch)
+    off = torch.from_numpy(off_h).cuda()
+    vals = sg.iota(n)
+    o = ss.make_options(seed=1)
+    ws = ss.alloc_workspace_batched(ss.OP_EQUAL, keys, off.view(torch.uint64), vals, o)
+    ko, vo = ss.semisort_equal_batched(keys, vals, off.view(torch.uint64), workspace=ws, options=o)
+    torch.cuda.synchronize()
+    assert ss.last_device_error(ws) == 0
+    del ws
+    ki, kk, vv = keys.view(torch.int64), ko.view(torch.int64), vo.view(torch.int64)
+    pos_inst = torch.searchsorted(off, torch.arange(n, device="cuda", dtype=torch.int64), right=True) - 1
+    val_inst = torch.searchsorted(off, vv, right=True) - 1
+    assert bool((pos_inst == val_inst).all()), "a record left its instance"
+    del val_inst
+    assert bool((ki[vv] == kk).all()), "a record's key changed"
+    same = (kk[1:] == kk[:-1]) & (pos_inst[1:] == pos_inst[:-1])
+    assert bool((vv[1:][same] > vv[:-1][same]).all()), "equal keys out of input order"
+    runs = int((~same).sum().item()) + 1
+    # distinct (instance, key) pairs: sort by key, then stably by instance
+    order = torch.argsort(ki, stable=True)
+    inst_sorted = pos_inst[order]
+    o2 = torch.argsort(inst_sorted, stable=True)
+    ks, isx = ki[order][o2], inst_sorted[o2]
+    pairs = int(((ks[1:] != ks[:-1]) | (isx[1:] != isx[:-1])).sum().item()) + 1
+    assert runs == pairs, "equal keys not contiguous within an instance"
