@@ -167,6 +167,23 @@ def alg_bytes(st: dict) -> int:
     return 40 * dist + 32 * st.get("refined", 0) + 32 * st.get("copied", 0)
 
 
+def max_over_ranks(ms, world, device):
+    """The slowest rank's time: with N replicas, the job ends with the last one."""
+    if world <= 1:
+        return ms
+    import torch
+    import torch.distributed as dist
+    t = torch.tensor([ms], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def job_throughput(world, n, steps, ms):
+    """Whole-job records per second (Grec/s): every replica processes n
+    records per step, all within the slowest rank's time."""
+    return world * n * steps / (ms / 1000.0) / 1e9
+
+
 def dram_traffic_per_launch(n):
     """DRAM bytes (read + write) of one distribute.L0 launch on n records,
     from the committed ncu counters scaled by records; None when the kernel
@@ -533,13 +550,10 @@ def main():
     torch.cuda.synchronize()
     clk = clocks.stop()
     elapsed_ms = ev0.elapsed_time(ev1)
-    if world > 1:
-        t = torch.tensor([elapsed_ms], device="cuda")
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        elapsed_ms = float(t.item())
+    elapsed_ms = max_over_ranks(elapsed_ms, world, "cuda")
     assert ss.last_device_error(ws) == 0
 
-    value = world * n * args.steps / (elapsed_ms / 1000.0) / 1e9
+    value = job_throughput(world, n, args.steps, elapsed_ms)
     peak, peak_kind = load_peaks()
     dom_ms = [t for t in dominant if t == t]
     dom_avg = sum(dom_ms) / len(dom_ms) if dom_ms else float("nan")
