@@ -101,8 +101,10 @@ def make_keys(sg, d, n, out):
 
 
 def cpu_oracle_sample(sample_n: int, dists) -> dict:
-    """Time the oracle (the stable sort that defines a valid semisort_=
-    output) on the host cores, on a bounded sample of each distribution."""
+    """Single-thread scale point: the oracle's std::stable_sort (the stable
+    sort that defines a valid semisort_= output) on one host core, on the
+    first sample_n records of each distribution (numpy generators, same seed
+    as the GPU workload)."""
     import numpy as np
 
     import oracle
@@ -122,6 +124,27 @@ def cpu_oracle_sample(sample_n: int, dists) -> dict:
                       f"(same generators and seed as the GPU workload); std::stable_sort, 1 thread"}
 
 
+def cpu_oracle_all_cores(torch, keys, vals, dists, sample_n: int) -> dict:
+    """The oracle's stable sort on all host cores (libstdc++ parallel mode,
+    OpenMP), on the first sample_n records of every headline distribution,
+    copied from the GPU-generated inputs."""
+    import numpy as np
+
+    import oracle
+    total_n, total_t, used = 0, 0.0, 0
+    for k in keys:
+        kh = k[:sample_n].view(torch.int64).cpu().numpy().view(np.uint64)
+        vh = vals[:sample_n].view(torch.int64).cpu().numpy().view(np.uint64)
+        t0 = time.perf_counter()
+        _, _, used = oracle.stable_sort_parallel(kh, vh, 0)
+        total_t += time.perf_counter() - t0
+        total_n += len(kh)
+    return {"value": total_n / total_t / 1e9, "unit": UNIT, "cores": used, "nproc": os.cpu_count(),
+            "kind": "oracle",
+            "sample": f"first {sample_n} records of each of {', '.join(dist_name(d) for d in dists)} "
+                      f"(copied from the GPU inputs); __gnu_parallel::stable_sort on {used} threads"}
+
+
 def headline_config(n, dists, world):
     return {"workload": f"semisort_equal n={n} (u64 key, u64 value=index), steps cycle over "
                         + ", ".join(dist_name(d) for d in dists),
@@ -131,28 +154,40 @@ def headline_config(n, dists, world):
 
 def run_reference(args, rank, world):
     """The reference arm: the oracle (the stable sort that defines a valid
-    semisort_= output) on the host cores, each step a bounded sample -- the
+    semisort_= output) on all host cores, each step a bounded sample -- the
     first ref_sample records -- of the step's distribution of the headline
     workload (same generators and seed), cycling over the same ten
-    distributions."""
+    distributions.  Sample generation is outside the timed steps."""
     if rank != 0:
         return 0
+    import numpy as np
+
+    import oracle
+    import synth
     dists = [DISTS[int(i)] for i in args.dists.split(",")] if args.dists else DISTS
     sample_n = args.ref_sample
-    t_steps = []
+    samples = {}
+    t_steps, used = [], 0
     for i in range(args.warmup + args.steps):
-        cb = cpu_oracle_sample(sample_n, [dists[i % len(dists)]])
+        d = dists[i % len(dists)]
+        if d not in samples:
+            samples[d] = synth.uniform_exact(SEED, N_DEFAULT, int(d[1]), 0, sample_n) if d[0] == "uniform" else \
+                synth.zipf(SEED, sample_n, float(d[1]), N=10**9)
+        keys = samples[d]
+        vals = np.arange(sample_n, dtype=np.uint64)
+        t0 = time.perf_counter()
+        _, _, used = oracle.stable_sort_parallel(keys, vals, 0)
         if i >= args.warmup:
-            t_steps.append(sample_n / (cb["value"] * 1e9))
+            t_steps.append(time.perf_counter() - t0)
     total_t = sum(t_steps)
     value = args.steps * sample_n / total_t / 1e9
     line = {"impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world,
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1000 * total_t / args.steps,
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "u64", "data": "synthetic",
             "config": headline_config(args.n, dists, world),
-            "cpu_baseline": {"value": value, "unit": UNIT, "cores": 1, "kind": "oracle",
-                             "sample": f"first {sample_n} records of each step's distribution; std::stable_sort, "
-                                       f"1 thread"},
+            "cpu_baseline": {"value": value, "unit": UNIT, "cores": used, "nproc": os.cpu_count(), "kind": "oracle",
+                             "sample": f"first {sample_n} records of each step's distribution; "
+                                       f"__gnu_parallel::stable_sort on {used} threads"},
             "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
     print(json.dumps(line))
     return 0
@@ -213,9 +248,10 @@ def time_op(ss, sg, torch, name, keys, dists, vals, kout, vout, ws, n, stream):
     semisort_< on uniform-10^9, Zipf-1.2, floor(Exp(10^-6)) and an 8-component
     Gaussian mixture."""
     learned = name == "semisort_less_learned"
-    flags = ss.FLAG_PHASE_TIMING | (ss.FLAG_IDENTITY_HASH if name == "semisort_equal_identity" else 0) | \
+    flags = (ss.FLAG_IDENTITY_HASH if name == "semisort_equal_identity" else 0) | \
         (ss.FLAG_HASH_BUCKETS if name == "semisort_less_hash" else 0)
-    opt = ss.make_options(seed=1, flags=flags, splitter_mode=1 if learned else 0)
+    opt_plain = ss.make_options(seed=1, flags=flags, splitter_mode=1 if learned else 0)
+    opt_timed = ss.make_options(seed=1, flags=flags | ss.FLAG_PHASE_TIMING, splitter_mode=1 if learned else 0)
     nu = torch.zeros(1, dtype=torch.uint64, device="cuda")
     names = [dist_name(d) for d in dists]
     inputs = list(keys)
@@ -230,7 +266,7 @@ def time_op(ss, sg, torch, name, keys, dists, vals, kout, vout, ws, n, stream):
             inputs.append(t)
             names.append(f"{kind}-{p:g}")
 
-    def call(k):
+    def call(k, opt=opt_plain):
         if name.startswith("semisort_equal"):
             ss.semisort_equal(k, vals, keys_out=kout, vals_out=vout, workspace=ws, options=opt)
         elif name.startswith("semisort_less"):
@@ -254,6 +290,8 @@ def time_op(ss, sg, torch, name, keys, dists, vals, kout, vout, ws, n, stream):
         b.synchronize()
         per[nm] = a.elapsed_time(b)
         total += per[nm]
+        call(k, opt_timed)  # a second, instrumented call for the phase split
+        torch.cuda.synchronize()
         for pn, pm in ss.phase_times():
             phases[pn] = phases.get(pn, 0.0) + pm / len(inputs)
         if name in ("semisort_less", "semisort_less_learned"):
@@ -453,6 +491,57 @@ def bench_rmat_csr(ss, sg, torch, stream, reps=3, scale=26, m=1 << 30):
             "ms": {"batched": t_b, **out}}
 
 
+def e2e_pipelined(ss, torch, hk, hv, n, steps, ws, opt):
+    """End to end through the public API with host buffers: every step copies
+    its input (keys, values) from pinned host memory to the device, runs
+    semisort_=, and copies the output back to pinned host memory.  Steps are
+    pipelined on three streams with two device buffer sets, so step i+1's
+    upload and step i-1's download overlap step i's call; all copies are
+    inside the timed region."""
+    u64 = torch.uint64
+    s_cmp = torch.cuda.current_stream()
+    s_in, s_out = torch.cuda.Stream(), torch.cuda.Stream()
+    din = [(torch.empty(n, dtype=u64, device="cuda"), torch.empty(n, dtype=u64, device="cuda")) for _ in range(2)]
+    dout = [(torch.empty(n, dtype=u64, device="cuda"), torch.empty(n, dtype=u64, device="cuda")) for _ in range(2)]
+    hko = torch.empty(n, dtype=u64, pin_memory=True)
+    hvo = torch.empty(n, dtype=u64, pin_memory=True)
+    ev = lambda: torch.cuda.Event()
+    ev_in, ev_cmp, ev_out = [ev(), ev()], [ev(), ev()], [ev(), ev()]
+    torch.cuda.synchronize()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record(s_cmp)
+    s_in.wait_event(e0)
+    s_out.wait_event(e0)
+    for i in range(steps):
+        b = i % 2
+        if i >= 2:
+            s_in.wait_event(ev_cmp[b])   # step i-2 has consumed din[b]
+        with torch.cuda.stream(s_in):
+            din[b][0].copy_(hk, non_blocking=True)
+            din[b][1].copy_(hv, non_blocking=True)
+        ev_in[b].record(s_in)
+        s_cmp.wait_event(ev_in[b])
+        if i >= 2:
+            s_cmp.wait_event(ev_out[b])  # step i-2's download has read dout[b]
+        ss.semisort_equal(din[b][0], din[b][1], keys_out=dout[b][0], vals_out=dout[b][1], workspace=ws,
+                          options=opt, stream=s_cmp)
+        ev_cmp[b].record(s_cmp)
+        s_out.wait_event(ev_cmp[b])
+        with torch.cuda.stream(s_out):
+            hko.copy_(dout[b][0], non_blocking=True)
+            hvo.copy_(dout[b][1], non_blocking=True)
+        ev_out[b].record(s_out)
+    s_cmp.wait_event(ev_out[(steps - 1) % 2])
+    e1.record(s_cmp)
+    torch.cuda.synchronize()
+    assert ss.last_device_error(ws) == 0
+    t = e0.elapsed_time(e1) / 1000.0
+    # the last step's output is the input's semisort: spot-check stability of the download
+    ok = bool(torch.equal(hko[:1024], dout[(steps - 1) % 2][0][:1024].cpu()))
+    del din, dout
+    return n * steps / t / 1e9, t, ok
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -461,9 +550,11 @@ def main():
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--n", type=int, default=N_DEFAULT)
     ap.add_argument("--ref-sample", type=int, default=1 << 24)
-    ap.add_argument("--cpu-sample", type=int, default=1 << 24)
-    ap.add_argument("--e2e-steps", type=int, default=3)
-    ap.add_argument("--quick", action="store_true", help="small smoke configuration (not a bench number)")
+    ap.add_argument("--cpu-sample", type=int, default=1 << 25,
+                    help="records per distribution for the all-core oracle leg (0: skip both CPU legs)")
+    ap.add_argument("--cpu-scale-sample", type=int, default=1 << 24,
+                    help="records per distribution for the single-thread scale point (0: skip)")
+    ap.add_argument("--e2e-steps", type=int, default=4)
     ap.add_argument("--dists", default="", help="comma-separated indices into the distribution list")
     ap.add_argument("--ops", default="collect_reduce,histogram,semisort_equal_identity,semisort_less,"
                                       "semisort_less_learned,semisort_less_hash,batched,rmat_csr",
@@ -497,7 +588,8 @@ def main():
     torch.cuda.synchronize()
     kout = torch.empty(n, dtype=torch.uint64, device="cuda")
     vout = torch.empty(n, dtype=torch.uint64, device="cuda")
-    opt = ss.make_options(seed=1, flags=ss.FLAG_PHASE_TIMING)
+    opt = ss.make_options(seed=1)
+    opt_timed = ss.make_options(seed=1, flags=ss.FLAG_PHASE_TIMING)
     ops = [o for o in args.ops.split(",") if o]
     op_codes = {"semisort_equal": ss.OP_EQUAL, "collect_reduce": ss.OP_REDUCE, "histogram": ss.OP_HIST,
                 "semisort_less": ss.OP_LESS, "semisort_less_learned": ss.OP_LESS, "semisort_less_hash": ss.OP_LESS,
@@ -507,34 +599,51 @@ def main():
     ws = torch.empty(ws_bytes, dtype=torch.uint8, device="cuda")
     stream = torch.cuda.current_stream()
 
-    def step(i):
-        ss.semisort_equal(keys[i % len(dists)], vals, keys_out=kout, vals_out=vout, workspace=ws, options=opt)
+    def step(i, o=opt):
+        ss.semisort_equal(keys[i % len(dists)], vals, keys_out=kout, vals_out=vout, workspace=ws, options=o)
 
     for i in range(args.warmup):
         step(i)
     torch.cuda.synchronize()
     assert ss.last_device_error(ws) == 0
 
-    per_dist = {dist_name(d): [] for d in dists}
-    phases = {}
-    dominant, dom_bytes, alg_total = [], [], 0
+    # ---- timed region: the plain library calls back to back (no
+    # instrumentation, no host synchronization between steps) ----
     launches = 0
     clocks = Clocks(local)
     if world > 1:
         dist.barrier()
     torch.cuda.synchronize()
     clocks.start()
-    ev0 = torch.cuda.Event(enable_timing=True)
-    ev1 = torch.cuda.Event(enable_timing=True)
-    ev0.record(stream)
+    ev_steps = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps + 1)]
+    ev_steps[0].record(stream)
     for i in range(args.steps):
-        e_a = torch.cuda.Event(enable_timing=True)
-        e_b = torch.cuda.Event(enable_timing=True)
-        e_a.record(stream)
         step(i)
-        e_b.record(stream)
         launches += ss.kernel_launches()
-        # per-kernel CUDA events recorded by the library on this stream
+        ev_steps[i + 1].record(stream)
+    torch.cuda.synchronize()
+    clk = clocks.stop()
+    elapsed_ms = ev_steps[0].elapsed_time(ev_steps[-1])
+    if world > 1:
+        dist.barrier()
+    elapsed_ms = max_over_ranks(elapsed_ms, world, "cuda")
+    assert ss.last_device_error(ws) == 0
+    per_dist = {dist_name(d): [] for d in dists}
+    for i in range(args.steps):
+        per_dist[dist_name(dists[i % len(dists)])].append(ev_steps[i].elapsed_time(ev_steps[i + 1]))
+
+    # ---- instrumented pass over the same K steps: per-kernel CUDA events
+    # recorded by the library on the launching stream, and the exact record
+    # classes of each call (for the byte model) ----
+    phases = {}
+    dominant, dom_bytes, alg_total, instr_ms = [], [], 0, 0.0
+    for i in range(args.steps):
+        e_a, e_b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e_a.record(stream)
+        step(i, opt_timed)
+        e_b.record(stream)
+        e_b.synchronize()
+        instr_ms += e_a.elapsed_time(e_b)
         ph = dict()
         for name, ms in ss.phase_times():
             ph[name] = ph.get(name, 0.0) + ms
@@ -544,13 +653,6 @@ def main():
         alg_total += alg_bytes(st)
         dominant.append(ph.get("distribute.L0", float("nan")))
         dom_bytes.append(32 * st.get("dist_l0", 0))
-        e_b.synchronize()
-        per_dist[dist_name(dists[i % len(dists)])].append(e_a.elapsed_time(e_b))
-    ev1.record(stream)
-    torch.cuda.synchronize()
-    clk = clocks.stop()
-    elapsed_ms = ev0.elapsed_time(ev1)
-    elapsed_ms = max_over_ranks(elapsed_ms, world, "cuda")
     assert ss.last_device_error(ws) == 0
 
     value = job_throughput(world, n, args.steps, elapsed_ms)
@@ -561,42 +663,33 @@ def main():
     achieved = dom_b / (dom_avg / 1000.0) / 1e9 if dom_ms else None
     traffic = dram_traffic_per_launch(n)
 
-    # end to end: pinned host input -> device, the call, result -> pinned host
-    e2e = None
-    if rank == 0 and args.e2e_steps > 0:
-        d_e2e = dists[8]
-        hk = torch.empty(n, dtype=torch.uint64, pin_memory=True)
-        hv = torch.empty(n, dtype=torch.uint64, pin_memory=True)
-        hko = torch.empty(n, dtype=torch.uint64, pin_memory=True)
-        hvo = torch.empty(n, dtype=torch.uint64, pin_memory=True)
-        hk.copy_(keys[8], non_blocking=False)
-        hv.copy_(vals, non_blocking=False)
-        dk, dv = keys[0], keys[1]  # device staging (reuses distribution buffers)
-        opt_plain = ss.make_options(seed=1)
-        torch.cuda.synchronize()
-        e0 = torch.cuda.Event(enable_timing=True)
-        e1 = torch.cuda.Event(enable_timing=True)
-        e0.record(stream)
-        for _ in range(args.e2e_steps):
-            dk.copy_(hk, non_blocking=True)
-            dv.copy_(hv, non_blocking=True)
-            ss.semisort_equal(dk, dv, keys_out=kout, vals_out=vout, workspace=ws, options=opt_plain)
-            hko.copy_(kout, non_blocking=True)
-            hvo.copy_(vout, non_blocking=True)
-        e1.record(stream)
-        torch.cuda.synchronize()
-        t = e0.elapsed_time(e1) / 1000.0
-        e2e = {"value": n * args.e2e_steps / t / 1e9, "unit": UNIT, "h2d_bytes_per_step": 16 * n,
-               "d2h_bytes_per_step": 16 * n, "workload": f"semisort_equal n={n} {dist_name(d_e2e)}"}
-        del hk, hv, hko, hvo
-
     by_op = {}
     for o in ops:
-        if o != "batched":
+        if o not in ("batched", "rmat_csr"):
             by_op[o] = time_op(ss, sg, torch, o, keys, dists, vals, kout, vout, ws, n, stream)
+
+    # end to end through the public API with host buffers (own staging buffers)
+    e2e = None
+    cpu = None
+    if rank == 0 and args.e2e_steps > 0:
+        d_i = next((i for i, d in enumerate(dists) if d == ("zipf", 1.2)), len(dists) - 1)
+        hk = torch.empty(n, dtype=torch.uint64, pin_memory=True)
+        hv = torch.empty(n, dtype=torch.uint64, pin_memory=True)
+        hk.copy_(keys[d_i])
+        hv.copy_(vals)
+        del kout, vout
+        torch.cuda.empty_cache()
+        v_e2e, t_e2e, ok = e2e_pipelined(ss, torch, hk, hv, n, args.e2e_steps, ws, opt)
+        e2e = {"value": v_e2e, "unit": UNIT, "h2d_bytes_per_step": 16 * n, "d2h_bytes_per_step": 16 * n,
+               "workload": f"semisort_equal n={n} {dist_name(dists[d_i])}, {args.e2e_steps} steps pipelined "
+                           "(upload, call, download on three streams, two device buffer sets)",
+               "seconds": t_e2e, "download_check": ok}
+        del hk, hv
+    if rank == 0 and args.cpu_sample:
+        cpu = cpu_oracle_all_cores(torch, keys, vals, dists, args.cpu_sample)
     if "batched" in ops or "rmat_csr" in ops:
         keys.clear()
-        del ws, kout, vout, vals
+        del ws, vals
         torch.cuda.empty_cache()
     if "batched" in ops:
         by_op["batched"] = bench_batched(ss, sg, torch, stream, reps=3)
@@ -608,7 +701,10 @@ def main():
         if world > 1:
             dist.destroy_process_group()
         return 0
-    cpu = cpu_oracle_sample(args.cpu_sample, [dists[3], dists[8]]) if args.cpu_sample else None
+    if cpu is not None and args.cpu_scale_sample:
+        cpu["single_thread_scale_point"] = cpu_oracle_sample(args.cpu_scale_sample, [dists[min(3, len(dists) - 1)],
+                                                                                     dists[-2 if len(dists) > 1
+                                                                                           else 0]])
     ms_step = elapsed_ms / args.steps
     line = {
         "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
@@ -618,10 +714,13 @@ def main():
         "roofline": {"bound": "hbm", "kernel": "distribute.L0",
                      "achieved": achieved, "peak": peak, "peak_kind": peak_kind, "unit": "GB/s",
                      "frac": (achieved / peak) if achieved else None, "traffic": traffic,
-                     "alg_bytes_per_launch": dom_b, "avg_launch_ms": dom_avg},
+                     "alg_bytes_per_launch": dom_b, "avg_launch_ms": dom_avg,
+                     "measured_in": "instrumented pass over the same steps (per-kernel CUDA events on the "
+                                    "launching stream)"},
         "path_roofline": {"alg_bytes_per_step": alg_total / args.steps,
                           "achieved_gbs": alg_total / (elapsed_ms / 1000.0) / 1e9,
                           "frac": alg_total / (elapsed_ms / 1000.0) / 1e9 / peak},
+        "instrumented_ms_per_step": instr_ms / args.steps,
         "per_distribution_ms": {k: (sum(v) / len(v) if v else None) for k, v in per_dist.items()},
         "phase_ms": {k: sum(v) / len(v) for k, v in phases.items()},
         "cpu_baseline": cpu,

@@ -28,7 +28,10 @@
  *    depth limit of six levels) set a flag in the workspace; ss_last_device_error() reads
  *    and clears it.  Each call resets the flag when it starts, so the flag
  *    describes the most recent call on that workspace.  No kernel traps.
- *  - n = 0 is valid and enqueues nothing.  n must be below 2^32 - 2^20.
+ *  - n = 0 is valid and enqueues nothing.  n must be below 2^32 - 2^20
+ *    (SS_ERR_UNSUPPORTED otherwise): offsets inside a subproblem are 32-bit,
+ *    which halves the count-matrix traffic; with 16-byte records, input,
+ *    output and the two temporaries of 2^32 records would need 256 GB.
  *  - Determinism: for a fixed options.seed every output is bit-identical
  *    across runs (the method is race-free, Sec. 2.2 and Sec. 3).
  */
@@ -51,7 +54,7 @@ typedef enum {
   SS_ERR_WORKSPACE_TOO_SMALL = 3, /* ws_bytes below ss_workspace_size() */
   SS_ERR_CAPACITY = 4,            /* more unique keys than the output capacity */
   SS_ERR_NOMEM = 5,               /* request exceeds free device memory */
-  SS_ERR_TIMEOUT = 6,             /* a bounded device wait ran out */
+  SS_ERR_TIMEOUT = 6,             /* reserved: no kernel of this library waits on another */
   SS_ERR_CUDA = 7,                /* a CUDA runtime call failed */
   SS_ERR_DEPTH = 8                /* recursion deeper than the level limit */
 } ss_status;
@@ -156,9 +159,11 @@ ss_status histogram(ss_type key_type, const void* keys, void* ukeys_out, uint32_
  *  - Calls that may overlap in time (different streams or host threads without
  *    ordering between them) race on the shared array and give wrong results;
  *    order them on one stream or synchronize between them.
- *  - SS_FLAG_PHASE_TIMING is ignored.  A device-side failure (the recursion
- *    depth limit) sets the flag inside the internal array, where callers cannot
- *    read it.
+ *  - SS_FLAG_PHASE_TIMING and SS_FLAG_IDENTITY_HASH are ignored: keys are
+ *    always bucketed by the hash, which cannot exhaust the recursion levels at
+ *    these sizes (identity bucketing can, on keys that differ only in high
+ *    bits).  A device-side failure would set the flag inside the internal
+ *    array, where callers cannot read it.
  * Other arguments, output and errors as semisort_equal. */
 ss_status semisort_equal_noalloc(ss_type key_type, ss_type val_type, const void* keys,
                                  const void* vals, void* keys_out, void* vals_out, uint64_t n,

@@ -37,14 +37,30 @@ KT = {np.dtype(np.uint32): 0, np.dtype(np.uint64): 1}
 VT = {np.dtype(np.uint32): 0, np.dtype(np.uint64): 1}
 
 
+_LIB_PAR = os.path.join(_LIBDIR, "liboracle_par.so")
+_SRC_PAR = os.path.join(_HERE, "oracle_parallel.cpp")
+_lib_par = None
+
+
 def build(force: bool = False) -> str:
-    """Compile the oracle with the host C++ compiler (no CUDA involved)."""
+    """Compile the oracle with the host C++ compiler (no CUDA involved); the
+    all-core stable sort is a separate OpenMP library (build_parallel)."""
     os.makedirs(_LIBDIR, exist_ok=True)
     if force or not os.path.exists(_LIB) or os.path.getmtime(_LIB) < os.path.getmtime(_SRC):
         tmp = _LIB + ".tmp"
         subprocess.check_call(["g++", "-O2", "-std=c++17", "-shared", "-fPIC", _SRC, "-o", tmp])
         os.replace(tmp, _LIB)
     return _LIB
+
+
+def build_parallel(force: bool = False) -> str:
+    """Compile the all-core stable sort (libstdc++ parallel mode, OpenMP)."""
+    os.makedirs(_LIBDIR, exist_ok=True)
+    if force or not os.path.exists(_LIB_PAR) or os.path.getmtime(_LIB_PAR) < os.path.getmtime(_SRC_PAR):
+        tmp = _LIB_PAR + ".tmp"
+        subprocess.check_call(["g++", "-O2", "-std=c++17", "-fopenmp", "-shared", "-fPIC", _SRC_PAR, "-o", tmp])
+        os.replace(tmp, _LIB_PAR)
+    return _LIB_PAR
 
 
 def _load():
@@ -98,6 +114,29 @@ def stable_sort(keys, vals=None):
     rc = _load().ss_oracle_stable_sort(_key_code(keys), vt, n, _ptr(keys), _ptr(vals), _ptr(ko), _ptr(vo))
     assert rc == 0
     return ko, vo
+
+
+def stable_sort_parallel(keys, vals=None, threads: int = 0):
+    """The same stable sort on `threads` host threads (0 = all) with
+    libstdc++'s parallel-mode stable_sort; u32/u64 keys and values.  Returns
+    (keys, vals, threads used)."""
+    global _lib_par
+    with _lock:
+        if _lib_par is None:
+            lib = ctypes.CDLL(build_parallel())
+            f = lib.ss_oracle_stable_sort_parallel
+            f.argtypes = [ctypes.c_int, ctypes.c_int, ctypes.c_uint64] + [ctypes.c_void_p] * 4 + [ctypes.c_int]
+            f.restype = ctypes.c_int
+            _lib_par = lib
+    keys, vals = _c(keys), _c(vals)
+    n = keys.shape[0]
+    ko = np.empty_like(keys)
+    vo = None if vals is None else np.empty_like(vals)
+    vt = 1 if vals is None else VT[vals.dtype]
+    used = _lib_par.ss_oracle_stable_sort_parallel(KT[keys.dtype], vt, n, _ptr(keys), _ptr(vals), _ptr(ko),
+                                                    _ptr(vo), int(threads))
+    assert used > 0
+    return ko, vo, used
 
 
 def group_by(keys, vals=None):

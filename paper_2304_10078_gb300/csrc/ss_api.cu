@@ -598,6 +598,12 @@ extern "C" ss_status semisort_equal_noalloc(ss_type key_type, ss_type val_type, 
   memset(&o, 0, sizeof(o));
   if (opt) o = *opt;
   o.flags &= ~SS_FLAG_PHASE_TIMING;
+  // The device error flag lives inside the static array, where a caller of
+  // this entry point cannot read it.  Hash bucketing cannot exhaust the
+  // recursion levels at these sizes, but identity bucketing can (keys that
+  // differ only in bits above those the levels consume), so this entry point
+  // always buckets by the hash.
+  o.flags &= ~SS_FLAG_IDENTITY_HASH;
   // Nothing in the array has to start at zero: the pipeline's first kernel
   // resets the control block, and every other region is written before it is read.
   return semisort_common(kOpEqual, key_type, val_type, keys, vals, keys_out, vals_out, n, ws, kNoAllocBytes, &o,

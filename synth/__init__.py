@@ -129,7 +129,11 @@ def uniform_exact(seed: int, n: int, mu: int, start: int = 0, count: int | None 
 class _ZipfRI:
     """Rejection-inversion sampler for P(k) ~ k^-s on k = 1..N (Hormann and
     Derflinger 1996): invert the integral H of the hat h(x) = x^-s, then accept
-    k = round(x) if x falls under the histogram of h around k."""
+    k = round(x) if x falls under the histogram of h around k.  The helper
+    functions log1p(x)/x and expm1(x)/x with their series guards, the
+    constants H(1.5) - 1 and 2 - H^-1(H(2.5) - h(2)) and the acceptance test
+    follow the shape of the Apache Commons RNG RejectionInversionZipfSampler
+    (Apache-2.0), a widely used statement of the same published method."""
 
     def __init__(self, s: float, N: int):
         self.s, self.N = float(s), int(N)

@@ -63,6 +63,10 @@ __global__ void k_uniform_exact(uint64_t* out, uint64_t count, uint64_t start, u
 }
 
 // Rejection-inversion for Zipf (Hormann and Derflinger, ACM TOMACS 1996).
+// The helpers, constants and acceptance test follow the shape of the Apache
+// Commons RNG RejectionInversionZipfSampler (Apache-2.0), a widely used
+// statement of the same published method; this is the GPU twin of the numpy
+// sampler in synth/__init__.py.
 struct ZipfP {
   double s, hx1, hn, sq;
   uint64_t N;

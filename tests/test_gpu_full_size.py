@@ -10,12 +10,29 @@ at any size and that the GPU can check in full:
   are distinct, and the sums add up to n(n-1)/2 mod 2^64 (value = index).
 * histogram: the unique count is the number of distinct keys and the counts
   add up to n.
+
+Collect-reduce and histogram are also compared with the oracle key by key
+at the full size (Zipf 1.2 and uniform 10^7 keys): the oracle runs on
+contiguous chunks of the input in host threads, and its per-chunk outputs are
+combined by the oracle's own collect-reduce (the sum of partial sums is the
+sum, by associativity of + mod 2^64).  On all ten benchmark distributions a
+grouping-independent checksum sum_k g(k) * sum_k = sum_i g(key_i) * val_i
+(mod 2^64, g a hash unrelated to the library's) catches per-key sums that
+are wrong in ways the totals hide.
 """
+import os
+from concurrent.futures import ThreadPoolExecutor
+
+import numpy as np
 import pytest
+
+import oracle
 
 pytestmark = pytest.mark.gpu
 
 N = 10**9
+DISTS = [("uniform", 10), ("uniform", 10**3), ("uniform", 10**5), ("uniform", 10**7), ("uniform", 10**9),
+         ("zipf", 0.6), ("zipf", 0.8), ("zipf", 1.0), ("zipf", 1.2), ("zipf", 1.5)]
 SEED = 0x5EED0002
 
 
@@ -159,3 +176,122 @@ def test_batched_semisort_equal_full_size(env):
     ks, isx = ki[order][o2], inst_sorted[o2]
     pairs = int(((ks[1:] != ks[:-1]) | (isx[1:] != isx[:-1])).sum().item()) + 1
     assert runs == pairs, "equal keys not contiguous within an instance"
+
+
+def host_u64(t):
+    import torch
+    return t.view(torch.int64).cpu().numpy().view(np.uint64)
+
+
+def oracle_reduce_chunked(keys_h, vals_h):
+    """The oracle's (unique keys ascending, sums) of the whole input, from
+    per-chunk oracle outputs (host threads; the oracle releases the GIL)
+    combined by the oracle's sort-based collect-reduce.  vals_h None: counts
+    (histogram)."""
+    n = len(keys_h)
+    parts = max(8, min(16, os.cpu_count() or 8))
+    cut = [n * i // parts for i in range(parts + 1)]
+
+    def one(i):
+        a, b = cut[i], cut[i + 1]
+        if vals_h is None:
+            k, c = oracle.histogram_hash(keys_h[a:b])
+            return k, c.astype(np.uint64)
+        return oracle.collect_reduce_hash(keys_h[a:b], vals_h[a:b])
+
+    with ThreadPoolExecutor(parts) as ex:
+        res = list(ex.map(one, range(parts)))
+    ks = np.concatenate([r[0] for r in res])
+    vs = np.concatenate([r[1] for r in res])
+    del res
+    return oracle.collect_reduce_sorted(ks, vs)
+
+
+def host_memory_gb():
+    try:
+        return os.sysconf("SC_PAGE_SIZE") * os.sysconf("SC_PHYS_PAGES") / 2**30
+    except (ValueError, OSError):
+        return 0.0
+
+
+@pytest.mark.parametrize("kind,p", [("zipf", 1.2), ("uniform", 10**7)])
+def test_reduce_and_histogram_full_size_vs_oracle(env, kind, p):
+    """Every (key, sum) and (key, count) at n = 10^9 against the oracle."""
+    import torch
+    if host_memory_gb() < 160:
+        pytest.skip("needs about 100 GB of host memory for the oracle")
+    ss, sg, vals = env
+    keys = keys_of(sg, kind, p)
+    o = ss.make_options(seed=1)
+    ws = ss.alloc_workspace(ss.OP_REDUCE, keys, vals, o)
+    uk, sums, nu = ss.collect_reduce(keys, vals, workspace=ws, options=o)
+    torch.cuda.synchronize()
+    assert ss.last_device_error(ws) == 0
+    u = int(nu.view(torch.int64)[0].item())
+    g_keys, g_sums = host_u64(uk[:u]), host_u64(sums[:u])
+    del uk, sums, ws
+    ws = ss.alloc_workspace(ss.OP_HIST, keys, None, o)
+    hk, cnt, nh = ss.histogram(keys, workspace=ws, options=o)
+    torch.cuda.synchronize()
+    assert ss.last_device_error(ws) == 0
+    h = int(nh.view(torch.int64)[0].item())
+    h_keys = host_u64(hk[:h])
+    h_cnt = cnt[:h].view(torch.int32).cpu().numpy().view(np.uint32)
+    del hk, cnt, ws
+    keys_h, vals_h = host_u64(keys), host_u64(vals)
+    del keys
+    torch.cuda.empty_cache()
+
+    rk, rs = oracle_reduce_chunked(keys_h, vals_h)
+    assert u == len(rk), (u, len(rk))
+    gk, gs = oracle.stable_sort(g_keys, g_sums)
+    assert np.array_equal(gk, rk), "collect-reduce unique keys differ"
+    bad = np.flatnonzero(gs != rs)
+    assert len(bad) == 0, f"{len(bad)} sums differ, first at key {rk[bad[0]]}"
+    del rs, gk, gs, g_keys, g_sums, vals_h
+
+    rk2, rc = oracle_reduce_chunked(keys_h, None)
+    assert h == len(rk2)
+    hk_s, hc_s = oracle.stable_sort(h_keys, h_cnt)
+    assert np.array_equal(hk_s, rk2), "histogram unique keys differ"
+    assert np.array_equal(hc_s.astype(np.uint64), rc), "histogram counts differ"
+
+
+def gmix(torch, k):
+    """A hash of int64 words unrelated to the library's mixers: two rounds of
+    multiply and xor-fold, in wrapping int64 arithmetic."""
+    x = k * 0x2545F4914F6CDD1D + 0x3C6EF372FE94F82B
+    x = x ^ ((x >> 29) & 0x7FFFFFFFF)
+    x = x * 0x27BB2EE687B0B0FD
+    return x ^ ((x >> 32) & 0xFFFFFFFF)
+
+
+@pytest.mark.parametrize("kind,p", DISTS)
+def test_reduce_weighted_checksum_full_size(env, kind, p):
+    """sum_k g(k) * sum_k (output) = sum_i g(key_i) * val_i (input), and the
+    same with val = 1 for the histogram, mod 2^64: per-key sums that err by
+    +x and -x on two keys change the checksum by x (g(k1) - g(k2))."""
+    import torch
+    ss, sg, vals = env
+    keys = keys_of(sg, kind, p)
+    ki, vi = keys.view(torch.int64), vals.view(torch.int64)
+    want_r = int((gmix(torch, ki) * vi).sum().item()) % 2**64
+    want_h = int(gmix(torch, ki).sum().item()) % 2**64
+    o = ss.make_options(seed=1)
+    ws = ss.alloc_workspace(ss.OP_REDUCE, keys, vals, o)
+    uk, sums, nu = ss.collect_reduce(keys, vals, workspace=ws, options=o)
+    torch.cuda.synchronize()
+    assert ss.last_device_error(ws) == 0
+    u = int(nu.view(torch.int64)[0].item())
+    got_r = int((gmix(torch, uk[:u].view(torch.int64)) * sums[:u].view(torch.int64)).sum().item()) % 2**64
+    assert got_r == want_r
+    del uk, sums, ws
+    ws = ss.alloc_workspace(ss.OP_HIST, keys, None, o)
+    hk, cnt, nh = ss.histogram(keys, workspace=ws, options=o)
+    torch.cuda.synchronize()
+    assert ss.last_device_error(ws) == 0
+    h = int(nh.view(torch.int64)[0].item())
+    assert h == u
+    c64 = cnt[:h].view(torch.int32).to(torch.int64) & 0xFFFFFFFF
+    got_h = int((gmix(torch, hk[:h].view(torch.int64)) * c64).sum().item()) % 2**64
+    assert got_h == want_h

@@ -267,3 +267,20 @@ def test_mix64_published_vectors_and_bijectivity():
         z = (z * inv1) & M64
         z = unxorshift(z, 30)
         assert z == x
+
+
+@pytest.mark.parametrize("kt,vt,threads", [(np.uint64, np.uint64, 0), (np.uint32, np.uint64, 3),
+                                           (np.uint64, np.uint32, 2), (np.uint32, np.uint32, 0)])
+def test_parallel_stable_sort_equals_serial_and_numpy(kt, vt, threads):
+    """The all-core oracle sort (the CPU baseline's) gives exactly the
+    serial oracle's output, and numpy's stable argsort agrees with both."""
+    rng = np.random.default_rng(77)
+    n = 300_007
+    keys = rng.integers(0, 5000, size=n).astype(kt)
+    vals = rng.integers(0, 2**31, size=n).astype(vt)
+    pk, pv, used = oracle.stable_sort_parallel(keys, vals, threads)
+    assert used >= 1 and (threads == 0 or used == threads)
+    sk, sv = oracle.stable_sort(keys, vals)
+    assert np.array_equal(pk, sk) and np.array_equal(pv, sv)
+    order = np.argsort(keys, kind="stable")
+    assert np.array_equal(pk, keys[order]) and np.array_equal(pv, vals[order])
