@@ -1019,6 +1019,13 @@ __global__ void __launch_bounds__(1024) k_scan(Work w, LevelBufs lb) {
 // written): stable, and no two CTAs ever write the same slot (race-free).
 // Light records go to the level's temporary array (records), heavy records
 // straight to their final place.
+//
+// Latency hiding: the chunk after the current one is prefetched into L2 when
+// the current one starts, and its loads into registers are issued before the
+// current chunk's output phase, so the copy into shared memory that follows
+// waits for nothing.  Bucket runs of the ranked chunk are found in one pass
+// in blocked order with a suffix minimum over threads (no per-record loop
+// over neighbours).
 // ----------------------------------------------------------------------------
 constexpr int kDT = 256;
 constexpr int kDR = 16;
@@ -1051,10 +1058,9 @@ __device__ __forceinline__ RecT<K, V> read_src(const LevelBufs& lb, uint64_t i) 
 
 // Coalesced copy of `len` records starting at global index g into S; eight
 // independent loads per thread are in flight before the first store.
-template <int NT, class K, class V, class Src, int PER = 16>
+template <int NT, class K, class V, class Src, int PER = 16, int B = 8>
 __device__ __forceinline__ void load_chunk(RecT<K, V>* S, uint32_t len, Src src) {
   using Rec = RecT<K, V>;
-  constexpr int B = 8;
   for (uint32_t i0 = 0; i0 < len; i0 += B * NT) {
     Rec t[B];
 #pragma unroll
@@ -1070,6 +1076,29 @@ __device__ __forceinline__ void load_chunk(RecT<K, V>* S, uint32_t len, Src src)
   }
 }
 
+// L2 prefetch of records [start, start + len) of a level's source (one
+// prefetch per 128-byte line, every address inside the range).
+template <class K, class V>
+__device__ __forceinline__ void prefetch_src(const LevelBufs& lb, uint64_t start, uint32_t len) {
+  auto pf = [&](const void* p0, uint64_t bytes) {
+    const char* p = reinterpret_cast<const char*>(p0);
+    const uint32_t lines = (uint32_t)((bytes + 127) / 128);
+    for (uint32_t l = threadIdx.x; l < lines; l += blockDim.x) {
+      uint64_t off = (uint64_t)l * 128;
+      if (off >= bytes) off = bytes - 1;
+      asm volatile("prefetch.global.L2 [%0];" ::"l"(p + off));
+    }
+  };
+  if (len == 0) return;
+  if (lb.src_aos) {
+    pf(reinterpret_cast<const RecT<K, V>*>(lb.src_k) + start, (uint64_t)len * sizeof(RecT<K, V>));
+  } else {
+    pf(reinterpret_cast<const K*>(lb.src_k) + start, (uint64_t)len * sizeof(K));
+    if constexpr (!std::is_same<V, void>::value)
+      pf(reinterpret_cast<const V*>(lb.src_v) + start, (uint64_t)len * sizeof(V));
+  }
+}
+
 template <class K, class V, int OP, bool BIG>
 __global__ void __launch_bounds__(kDT, 2) k_distribute(Work w, LevelBufs lb) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
@@ -1078,12 +1107,58 @@ __global__ void __launch_bounds__(kDT, 2) k_distribute(Work w, LevelBufs lb) {
   constexpr int RB = sizeof(Rec);
   constexpr bool kVals = !std::is_same<V, void>::value;
   using VV = typename ValT<V>::type;
+  // records per thread carried in registers from one chunk to the next
+  constexpr int kPF = RB <= 16 ? kDR : kDR / 2;
   const uint32_t nt = w.ctrl->ntiles[lb.level];
   constexpr bool kMoveHeavy = (OP == kOpEqual || OP == kOpLess);
   Rec* dst = reinterpret_cast<Rec*>(lb.dst);
-  const int tid = threadIdx.x;
+  const int tid = threadIdx.x, lane = tid & 31, wid = tid >> 5;
   const uint32_t c0t = tid * kDR;
-  for (uint32_t t = blockIdx.x; t < nt; t += gridDim.x) {
+  uint32_t t = blockIdx.x;
+  if (t >= nt) return;
+
+  // A chunk moves global -> registers (issue) -> shared memory (commit); the
+  // issue of chunk c + 1 comes before chunk c's output phase, so its loads
+  // are in flight while chunk c is written out.
+  Rec R[kPF];
+  auto issue = [&](uint64_t base, uint32_t len) {
+#pragma unroll
+    for (int u = 0; u < kPF; ++u) {
+      const uint32_t i = u * kDT + tid;
+      Rec v{};
+      if (i < len) v = read_src<K, V>(lb, base + i);
+      R[u] = v;
+    }
+  };
+  auto commit = [&](uint64_t base, uint32_t len) {
+#pragma unroll
+    for (int u = 0; u < kPF; ++u) {
+      const uint32_t i = u * kDT + tid;
+      if (i < len) sm.S[sw<RB>(i)] = R[u];
+    }
+    for (uint32_t i = kPF * kDT + tid; i < len; i += kDT) sm.S[sw<RB>(i)] = read_src<K, V>(lb, base + i);
+  };
+  // the first non-empty tile at or after tile index u of this CTA's sequence
+  auto first_chunk = [&](uint32_t u, uint64_t* base, uint32_t* len) {
+    *base = 0;
+    *len = 0;
+    for (; u < nt; u += gridDim.x) {
+      const Tile tu = w.tiles[lb.level][u];
+      if (tu.len) {
+        *base = tu.start;
+        *len = tu.len < (uint32_t)kDCH ? tu.len : (uint32_t)kDCH;
+        return;
+      }
+    }
+  };
+  {
+    uint64_t b0;
+    uint32_t l0;
+    first_chunk(t, &b0, &l0);
+    issue(b0, l0);
+    commit(b0, l0);
+  }
+  for (; t < nt; t += gridDim.x) {
     const Tile tl = w.tiles[lb.level][t];
     const Seg sg = w.segs[lb.level][tl.seg];
     const uint32_t nl = sg.nl;
@@ -1101,9 +1176,18 @@ __global__ void __launch_bounds__(kDT, 2) k_distribute(Work w, LevelBufs lb) {
     const int passes = nb > 1024 ? 3 : nb > 32 ? 2 : 1;
     for (uint32_t c0 = 0; c0 < tl.len; c0 += kDCH) {
       const uint32_t clen = tl.len - c0 < (uint32_t)kDCH ? tl.len - c0 : (uint32_t)kDCH;
-      const uint64_t gbase = tl.start + c0;
-      load_chunk<kDT, K, V>(sm.S, clen, [&](uint32_t i) { return read_src<K, V>(lb, gbase + i); });
-      __syncthreads();
+      // the chunk that follows this one: the tile's next chunk, or the first
+      // chunk of this CTA's next tile
+      uint64_t nbase = 0;
+      uint32_t nlen = 0;
+      if (c0 + kDCH < tl.len) {
+        nbase = tl.start + c0 + kDCH;
+        nlen = tl.len - (c0 + kDCH) < (uint32_t)kDCH ? tl.len - (c0 + kDCH) : (uint32_t)kDCH;
+      } else {
+        first_chunk(t + gridDim.x, &nbase, &nlen);
+      }
+      __syncthreads();  // the chunk is in S; tables and cursors are loaded
+      prefetch_src<K, V>(lb, nbase, nlen);
       uint32_t bid[kDR], rk[kDR];
       // invalid slots get id 2^15 - 1: every 5-bit digit is 31, and as the last
       // items in blocked order they rank after every valid record
@@ -1134,12 +1218,53 @@ __global__ void __launch_bounds__(kDT, 2) k_distribute(Work w, LevelBufs lb) {
       if (passes > 1) pass(21);
       if (BIG && passes > 2) pass(26);
       __syncthreads();
+      // Bucket runs of the ranked chunk, found in blocked order: thread t
+      // looks at sorted positions c0t .. c0t + 15.  smask marks run starts,
+      // emask run starts and the chunk end (clen).  A run ends at the next
+      // marked position: in this thread's range, else the first marked
+      // position of a later thread (a suffix minimum over threads).
+      uint32_t smask = 0, emask = 0, fb = 0xFFFFu;
+      {
+        uint32_t prev = c0t > 0 ? sm.px[bpad(c0t - 1)] >> 16 : 0xFFFFFFFFu;
+#pragma unroll
+        for (int r = 0; r < kDR; ++r) {
+          const uint32_t p = c0t + r;
+          const uint32_t b = sm.px[bpad(p)] >> 16;
+          const bool st = p < clen && b != prev;
+          const bool en = st || p == clen;
+          smask |= st ? 1u << r : 0u;
+          emask |= en ? 1u << r : 0u;
+          prev = b;
+        }
+        if (emask) fb = c0t + (__ffs(emask) - 1);
+      }
+      uint32_t nf;  // first marked position of the threads after this one
+      {
+        uint32_t v = fb;
+#pragma unroll
+        for (int o = 1; o < 32; o <<= 1) {
+          const uint32_t u = __shfl_down_sync(kFull, v, o);
+          if (lane + o < 32) v = u < v ? u : v;
+        }
+        const uint32_t after = __shfl_down_sync(kFull, v, 1);
+        if (lane == 0) sm.rk.scan_tmp[wid] = v;
+        __syncthreads();
+        nf = lane < 31 ? after : 0xFFFFu;
+        for (int j = wid + 1; j < kDT / 32; ++j) {
+          const uint32_t y = sm.rk.scan_tmp[j];
+          nf = y < nf ? y : nf;
+        }
+        if (nf > clen) nf = clen;  // a full chunk's end lies past every thread's range
+      }
       // run starts: turn the bucket's running offset into the base of this chunk
-      for (uint32_t p = tid; p < clen; p += kDT) {
-        const uint32_t b = sm.px[bpad(p)] >> 16;
-        if (p == 0 || (sm.px[bpad(p - 1)] >> 16) != b) sm.cur[b] -= p;
+      for (uint32_t m = smask; m; m &= m - 1) {
+        const int r = __ffs(m) - 1;
+        const uint32_t p = c0t + r;
+        sm.cur[sm.px[bpad(p)] >> 16] -= p;
       }
       __syncthreads();
+      // the next chunk's loads are in flight during the output phase
+      issue(nbase, nlen);
       for (uint32_t p = tid; p < clen; p += kDT) {
         const uint32_t x = sm.px[bpad(p)];
         const uint32_t b = x >> 16;
@@ -1158,12 +1283,16 @@ __global__ void __launch_bounds__(kDT, 2) k_distribute(Work w, LevelBufs lb) {
       }
       __syncthreads();
       // run ends: the next chunk continues after this chunk's run
-      for (uint32_t p = tid; p < clen; p += kDT) {
-        const uint32_t b = sm.px[bpad(p)] >> 16;
-        if (p + 1 == clen || (sm.px[bpad(p + 1)] >> 16) != b) sm.cur[b] += p + 1;
+      for (uint32_t m = smask; m; m &= m - 1) {
+        const int r = __ffs(m) - 1;
+        const uint32_t p = c0t + r;
+        const uint32_t later = emask >> r >> 1;
+        const uint32_t e = later ? p + __ffs(later) : nf;
+        sm.cur[sm.px[bpad(p)] >> 16] += e;
       }
-      __syncthreads();
+      commit(nbase, nlen);
     }
+    __syncthreads();  // cursors of this tile are final before the next tile's
   }
 }
 
@@ -1354,7 +1483,7 @@ __device__ __forceinline__ void store_out(const Work& w, uint64_t pos, const Rec
 // output, eight independent loads per thread in flight.
 template <int NT, class K, class V>
 __device__ __forceinline__ void copy_item(const Work& w, const Item& it) {
-  constexpr int B = 8;
+  constexpr int B = 2;
   for (uint32_t i0 = 0; i0 < it.len; i0 += B * NT) {
     RecT<K, V> t[B];
 #pragma unroll
@@ -1368,6 +1497,32 @@ __device__ __forceinline__ void copy_item(const Work& w, const Item& it) {
       if (i < it.len) store_out<K, V>(w, it.start + i, t[u]);
     }
   }
+}
+
+// Stable rank of the window's items by bits [16, 16 + 5 passes) of g[] (at
+// most three passes): (id << 16 | index) ends up at rank in px.  The passes
+// are straight-line code with constant digit positions; a loop over a runtime
+// pass count keeps g[] and the rank's arrays in local memory.
+__device__ __forceinline__ void rank_window(typename RRank::Smem& rs, uint32_t* px, const uint32_t (&g)[kRR],
+                                            uint32_t passes, uint32_t c0t) {
+  {
+    uint32_t rk[kRR];
+    RRank::rank(rs, g, 16, rk);
+#pragma unroll
+    for (int r = 0; r < kRR; ++r) px[bpad(rk[r])] = g[r];
+  }
+  auto pass = [&](int shift) {
+    __syncthreads();
+    uint32_t x[kRR], rk[kRR];
+#pragma unroll
+    for (int r = 0; r < kRR; ++r) x[r] = px[bpad(c0t + r)];
+    RRank::rank(rs, x, shift, rk);
+#pragma unroll
+    for (int r = 0; r < kRR; ++r) px[bpad(rk[r])] = x[r];
+  };
+  if (passes > 1) pass(21);
+  if (passes > 2) pass(26);
+  __syncthreads();
 }
 
 template <class K, class V>
@@ -1394,10 +1549,11 @@ __global__ void __launch_bounds__(kRT, 2) k_finish_equal(Work w) {
     }
     uint32_t ts = 64;
     while (ts < 2 * m) ts <<= 1;
-    load_chunk<kRT, K, V>(sm.S, m, [&](uint32_t i) { return load_rec<K, V>(w, it.buf, it.start + i); });
+    auto ld = [&](uint32_t i) { return load_rec<K, V>(w, it.buf, it.start + i); };
+    load_chunk<kRT, K, V, decltype(ld), 16, 4>(sm.S, m, ld);
     for (uint32_t i = tid; i < ts; i += kRT) sm.u.table[i] = kEmpty;
     __syncthreads();
-    uint32_t slot2[kRR / 2];  // two 16-bit table slots per word
+    // the table slot of every record is parked in px until the labels are read
 #pragma unroll
     for (int r = 0; r < kRR; ++r) {
       const uint32_t c = c0t + r;
@@ -1420,10 +1576,7 @@ __global__ void __launch_bounds__(kRT, 2) k_finish_equal(Work w) {
           s = (s + 1) & (ts - 1);
         }
       }
-      if (r & 1)
-        slot2[r >> 1] |= s << 16;
-      else
-        slot2[r >> 1] = s;
+      sm.px[bpad(c)] = s;
     }
     __syncthreads();
     // first-occurrence labels (kept per record in px) -> group ids in
@@ -1432,7 +1585,7 @@ __global__ void __launch_bounds__(kRT, 2) k_finish_equal(Work w) {
 #pragma unroll
     for (int r = 0; r < kRR; ++r) {
       const uint32_t c = c0t + r;
-      const uint32_t lab = c < m ? sm.u.table[(slot2[r >> 1] >> ((r & 1) * 16)) & 0xFFFFu] : 0;
+      const uint32_t lab = c < m ? sm.u.table[sm.px[bpad(c)]] : 0;
       sm.px[bpad(c)] = lab;
       nfirst += (c < m && lab == c) ? 1u : 0u;
     }
@@ -1458,7 +1611,7 @@ __global__ void __launch_bounds__(kRT, 2) k_finish_equal(Work w) {
     __syncthreads();
     // stable LSD ranking by group id, 5 bits per pass; padding items get
     // group 0xFFF and, last in blocked order, rank after every record
-    uint32_t g[kRR], rk[kRR];
+    uint32_t g[kRR];
 #pragma unroll
     for (int r = 0; r < kRR; ++r) {
       const uint32_t c = c0t + r;
@@ -1467,16 +1620,7 @@ __global__ void __launch_bounds__(kRT, 2) k_finish_equal(Work w) {
     const uint32_t gbits = ceil_log2_u32(G) < 1 ? 1 : ceil_log2_u32(G);
     const uint32_t passes = (gbits + 4) / 5;
     __syncthreads();  // group ids read: px and the hash table region are free
-    for (uint32_t pz = 0; pz < passes; ++pz) {
-      RRank::rank(sm.u.rk, g, 16 + 5 * pz, rk);
-#pragma unroll
-      for (int r = 0; r < kRR; ++r) sm.px[bpad(rk[r])] = g[r];
-      __syncthreads();
-      if (pz + 1 < passes) {
-#pragma unroll
-        for (int r = 0; r < kRR; ++r) g[r] = sm.px[bpad(c0t + r)];
-      }
-    }
+    rank_window(sm.u.rk, sm.px, g, passes, c0t);
     for (uint32_t p = tid; p < m; p += kRT) store_out<K, V>(w, it.start + p, sm.S[sw<RB>(sm.px[bpad(p)] & 0xFFFFu)]);
     __syncthreads();
   }
@@ -1529,7 +1673,8 @@ __global__ void __launch_bounds__(kRT, 2) k_finish_less(Work w) {
       if (tid == 0) set_error(w.ctrl, 8);
       continue;
     }
-    load_chunk<kRT, K, V>(sm.S, m, [&](uint32_t i) { return load_rec<K, V>(w, it.buf, it.start + i); });
+    auto ld = [&](uint32_t i) { return load_rec<K, V>(w, it.buf, it.start + i); };
+    load_chunk<kRT, K, V, decltype(ld), 16, 4>(sm.S, m, ld);
     if (tid == 0) {
       sm.fallback = sizeof(K) > 8 ? 1u : 0u;
       atomicAdd((unsigned long long*)&w.ctrl->stats[5], (unsigned long long)m);
@@ -1575,24 +1720,14 @@ __global__ void __launch_bounds__(kRT, 2) k_finish_less(Work w) {
         __syncthreads();
         continue;
       }
-      uint32_t g[kRR], rk[kRR];
+      uint32_t g[kRR];
 #pragma unroll
       for (int r = 0; r < kRR; ++r) {
         const uint32_t c = c0t + r;
         const uint32_t ib = c < m ? (uint32_t)(((uint64_t)sm.S[sw<RB>(c)].k - lo) >> shift) : 0x7FFFu;
         g[r] = (ib << 16) | c;
       }
-      const uint32_t passes = (nbits + 4) / 5;
-      for (uint32_t pz = 0; pz < passes; ++pz) {
-        RRank::rank(sm.u.rk, g, 16 + 5 * pz, rk);
-#pragma unroll
-        for (int r = 0; r < kRR; ++r) sm.px[bpad(rk[r])] = g[r];
-        __syncthreads();
-        if (pz + 1 < passes) {
-#pragma unroll
-          for (int r = 0; r < kRR; ++r) g[r] = sm.px[bpad(c0t + r)];
-        }
-      }
+      rank_window(sm.u.rk, sm.px, g, (nbits + 4) / 5, c0t);
       // finish every run of equal buckets by a stable insertion sort on the key.
       // With shift 0 a bucket holds one key value: the rank is already the sort.
       // Otherwise look for an out-of-order neighbour first (in parallel).
