@@ -219,19 +219,34 @@ def job_throughput(world, n, steps, ms):
     return world * n * steps / (ms / 1000.0) / 1e9
 
 
+DIST_REGION = ("paper_2304_10078_gb300/csrc/ss_kernels.cuh",
+               "// distribute: the second pass of Blocked Distributing",
+               "static __global__ void __launch_bounds__(1024) k_scan_items")
+
+
+def kernel_source_hash():
+    """sha256 of the source the distribute kernel is built from: its section of
+    the kernels file (the kernel and its helpers) and the shared primitives."""
+    import hashlib
+    h = hashlib.sha256()
+    path, start, end = DIST_REGION
+    with open(os.path.join(ROOT, path)) as f:
+        text = f.read()
+    a = text.index(start)
+    h.update(text[a:text.index(end, a)].encode())
+    with open(os.path.join(ROOT, "paper_2304_10078_gb300/csrc/ss_common.cuh"), "rb") as f:
+        h.update(f.read())
+    return h.hexdigest()
+
+
 def dram_traffic_per_launch(n):
     """DRAM bytes (read + write) of one distribute.L0 launch on n records,
-    from the committed ncu counters scaled by records; None when the kernel
-    sources changed after the counters were taken."""
-    import hashlib
+    from the committed ncu counters scaled by records; None when the kernel's
+    source changed after the counters were taken."""
     try:
         with open(os.path.join(ROOT, "profiles", "traffic.json")) as f:
             t = json.load(f)["distribute.L0"]
-        h = hashlib.sha256()
-        for p in t["kernel_sources"]:
-            with open(os.path.join(ROOT, p), "rb") as f:
-                h.update(f.read())
-        if h.hexdigest() != t["kernel_sources_sha256"]:
+        if kernel_source_hash() != t["kernel_source_sha256"]:
             return None
         return t["bytes_per_record"] * n
     except (OSError, KeyError, ValueError):
@@ -249,7 +264,8 @@ def time_op(ss, sg, torch, name, keys, dists, vals, kout, vout, ws, n, stream):
     Gaussian mixture."""
     learned = name == "semisort_less_learned"
     flags = (ss.FLAG_IDENTITY_HASH if name == "semisort_equal_identity" else 0) | \
-        (ss.FLAG_HASH_BUCKETS if name == "semisort_less_hash" else 0)
+        (ss.FLAG_HASH_BUCKETS if name == "semisort_less_hash" else 0) | \
+        (ss.FLAG_SWAP_OUTPUT if name == "semisort_equal_swap" else 0)
     opt_plain = ss.make_options(seed=1, flags=flags, splitter_mode=1 if learned else 0)
     opt_timed = ss.make_options(seed=1, flags=flags | ss.FLAG_PHASE_TIMING, splitter_mode=1 if learned else 0)
     nu = torch.zeros(1, dtype=torch.uint64, device="cuda")
@@ -297,8 +313,8 @@ def time_op(ss, sg, torch, name, keys, dists, vals, kout, vout, ws, n, stream):
         if name in ("semisort_less", "semisort_less_learned"):
             st = ss.stats(ws)
             balance[nm] = {"splitters": ["sampled", "learned", "learned rejected"][st["l0_splitters"]],
-                           "max_light_bucket_over_mean": st["l0_max_light_bucket"] / (n / 2048.0),
-                           "records_at_level3": st["dist_l2"]}
+                           "max_light_bucket_over_mean": st["l0_max_light_bucket"] / (n / max(1, st["l0_light_buckets"])),
+                           "records_at_level3": st["dist_l2"], "learn_steps": st["learn_steps"]}
     err = ss.last_device_error(ws)
     del extra
     out = {"value": n * len(inputs) / (total / 1000.0) / 1e9, "unit": UNIT, "device_error": err,
@@ -447,11 +463,12 @@ def bench_rmat_csr(ss, sg, torch, stream, reps=3, scale=26, m=1 << 30):
     nu = torch.zeros(parts, dtype=torch.uint64, device="cuda")
     oo = torch.zeros(parts + 1, dtype=torch.uint64, device="cuda")
     plain = ss.make_options(seed=1)
-    ws_l = ss.alloc_workspace_batched(ss.OP_LESS, src, off, dst, plain)
+    learned_b = ss.make_options(seed=1, splitter_mode=1)
+    ws_l = ss.alloc_workspace_batched(ss.OP_LESS, src, off, dst, learned_b)
     ws_h = ss.alloc_workspace_batched(ss.OP_HIST, src, off, None, plain)
 
-    def batched():
-        ss.semisort_less_batched(src, dst, off, keys_out=ks, vals_out=vs, workspace=ws_l, options=plain)
+    def batched(opt=plain):
+        ss.semisort_less_batched(src, dst, off, keys_out=ks, vals_out=vs, workspace=ws_l, options=opt)
         ss.histogram_batched(src, off, capacity=m, ukeys_out=uk, counts_out=cnt, num_unique=nu, out_offsets=oo,
                              workspace=ws_h, options=plain)
 
@@ -468,6 +485,9 @@ def bench_rmat_csr(ss, sg, torch, stream, reps=3, scale=26, m=1 << 30):
 
     t_b = timed(batched, reps)
     assert ss.last_device_error(ws_l) == 0 and ss.last_device_error(ws_h) == 0
+    t_bl = timed(lambda: batched(learned_b), reps)
+    assert ss.last_device_error(ws_l) == 0
+    kept = ss.stats(ws_l)["l0_max_sample_range"]
     del ws_l, ws_h
     big = int(np.max(np.diff(off_h)))
     learned = ss.make_options(seed=1, splitter_mode=1)
@@ -485,10 +505,83 @@ def bench_rmat_csr(ss, sg, torch, stream, reps=3, scale=26, m=1 << 30):
         out[mode] = timed(per_part, 1)
         assert ss.last_device_error(w1l) == 0
     return {"workload": f"R-MAT scale {scale}, {m} edges (u32 src, u32 dst), 64 partitions of sizes 2^U[0,4]",
-            "unit": UNIT, "batched": m / (t_b / 1000) / 1e9,
+            "unit": UNIT, "batched": m / (t_b / 1000) / 1e9, "batched_learned": m / (t_bl / 1000) / 1e9,
+            "batched_learned_partitions_kept_model": kept,
             "per_partition_sampled": m / (out["per_partition_sampled"] / 1000) / 1e9,
             "per_partition_learned": m / (out["per_partition_learned"] / 1000) / 1e9,
-            "ms": {"batched": t_b, **out}}
+            "ms": {"batched": t_b, "batched_learned": t_bl, **out}}
+
+
+SWEEP_DISTS = [("zipf", 1.2), ("uniform", 10**7)]
+
+
+def bench_sweeps(ss, sg, torch, stream, reps=3):
+    """The paper's two scaling experiments (Sec. 5, input size scalability and
+    varying key lengths) for semisort_= on one GPU:
+    * input size: n = 10^7 .. 10^9 (u64 key, u64 value = index);
+    * key width at n = 10^9: 32-bit keys with 32-bit values, 64-bit keys with
+      64-bit values, 128-bit keys with 64-bit values (the library has no
+      128-bit value type).  32-bit keys are the high halves of the 64-bit
+      keys; a 128-bit key is (64-bit key, its SplitMix64 mix), so distinct
+      64-bit keys stay distinct.
+    Zipf 1.2 and uniform 10^7 (the paper's representative distributions).
+    Device time of one call, median of `reps`, inputs resident in HBM."""
+    out = {"unit": UNIT, "input_size": {}, "key_width": {}}
+
+    def timed(fn):
+        fn()
+        ts = []
+        for _ in range(reps):
+            a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            a.record(stream)
+            fn()
+            b.record(stream)
+            b.synchronize()
+            ts.append(a.elapsed_time(b))
+        return statistics.median(ts)
+
+    for d in SWEEP_DISTS:
+        row = {}
+        for n in (10**7, 3 * 10**7, 10**8, 3 * 10**8, 10**9):
+            k = make_keys(sg, d, n, None)
+            v = sg.iota(n)
+            ko, vo = torch.empty_like(k), torch.empty_like(v)
+            ws = ss.alloc_workspace(ss.OP_EQUAL, k, v, ss.make_options(seed=1))
+            ms = timed(lambda: ss.semisort_equal(k, v, keys_out=ko, vals_out=vo, workspace=ws,
+                                                 options=ss.make_options(seed=1)))
+            assert ss.last_device_error(ws) == 0
+            row[str(n)] = n / (ms / 1000) / 1e9
+            del k, v, ko, vo, ws
+            torch.cuda.empty_cache()
+        out["input_size"][dist_name(d)] = row
+    n = 10**9
+    for d in SWEEP_DISTS:
+        row = {}
+        k64 = make_keys(sg, d, n, None)
+        for width in (32, 64, 128):
+            if width == 32:
+                k = (k64.view(torch.int64) >> 32).to(torch.int32).view(torch.uint32)
+                v = sg.iota(n).view(torch.int64).to(torch.int32).view(torch.uint32)
+            elif width == 64:
+                k, v = k64, sg.iota(n)
+            else:
+                hi = ss.hash_u64(k64, 0x5EED)
+                k = torch.stack([k64.view(torch.int64), hi.view(torch.int64)], dim=1).view(torch.uint64)
+                v = sg.iota(n)
+            ko, vo = torch.empty_like(k), torch.empty_like(v)
+            ws = ss.alloc_workspace(ss.OP_EQUAL, k, v, ss.make_options(seed=1))
+            ms = timed(lambda: ss.semisort_equal(k, v, keys_out=ko, vals_out=vo, workspace=ws,
+                                                 options=ss.make_options(seed=1)))
+            assert ss.last_device_error(ws) == 0
+            row[f"{width}-bit"] = n / (ms / 1000) / 1e9
+            del k, v, ko, vo, ws
+            torch.cuda.empty_cache()
+        out["key_width"][dist_name(d)] = row
+        del k64
+        torch.cuda.empty_cache()
+    out["workload"] = ("semisort_= (value = index); input sizes 1e7..1e9 with u64/u64; key widths at n=1e9: "
+                       "u32/u32, u64/u64, u128/u64; distributions " + ", ".join(dist_name(d) for d in SWEEP_DISTS))
+    return out
 
 
 def e2e_pipelined(ss, torch, hk, hv, n, steps, ws, opt):
@@ -556,8 +649,9 @@ def main():
                     help="records per distribution for the single-thread scale point (0: skip)")
     ap.add_argument("--e2e-steps", type=int, default=4)
     ap.add_argument("--dists", default="", help="comma-separated indices into the distribution list")
-    ap.add_argument("--ops", default="collect_reduce,histogram,semisort_equal_identity,semisort_less,"
-                                      "semisort_less_learned,semisort_less_hash,batched,rmat_csr",
+    ap.add_argument("--ops", default="collect_reduce,histogram,semisort_equal_identity,semisort_equal_swap,"
+                                      "semisort_less,"
+                                      "semisort_less_learned,semisort_less_hash,batched,rmat_csr,sweeps",
                     help="further operations timed after the headline (empty: none)")
     args = ap.parse_args()
 
@@ -593,7 +687,7 @@ def main():
     ops = [o for o in args.ops.split(",") if o]
     op_codes = {"semisort_equal": ss.OP_EQUAL, "collect_reduce": ss.OP_REDUCE, "histogram": ss.OP_HIST,
                 "semisort_less": ss.OP_LESS, "semisort_less_learned": ss.OP_LESS, "semisort_less_hash": ss.OP_LESS,
-                "semisort_equal_identity": ss.OP_EQUAL}
+                "semisort_equal_identity": ss.OP_EQUAL, "semisort_equal_swap": ss.OP_EQUAL}
     ws_bytes = max(ss.workspace_size(op_codes[o], ss.SS_U64, ss.SS_U64, n, opt)
                    for o in ["semisort_equal"] + ops if o in op_codes)
     ws = torch.empty(ws_bytes, dtype=torch.uint8, device="cuda")
@@ -665,7 +759,7 @@ def main():
 
     by_op = {}
     for o in ops:
-        if o not in ("batched", "rmat_csr"):
+        if o not in ("batched", "rmat_csr", "sweeps"):
             by_op[o] = time_op(ss, sg, torch, o, keys, dists, vals, kout, vout, ws, n, stream)
 
     # end to end through the public API with host buffers (own staging buffers)
@@ -687,7 +781,7 @@ def main():
         del hk, hv
     if rank == 0 and args.cpu_sample:
         cpu = cpu_oracle_all_cores(torch, keys, vals, dists, args.cpu_sample)
-    if "batched" in ops or "rmat_csr" in ops:
+    if "batched" in ops or "rmat_csr" in ops or "sweeps" in ops:
         keys.clear()
         del ws, vals
         torch.cuda.empty_cache()
@@ -696,6 +790,9 @@ def main():
         torch.cuda.empty_cache()
     if "rmat_csr" in ops:
         by_op["rmat_csr"] = bench_rmat_csr(ss, sg, torch, stream, reps=3)
+        torch.cuda.empty_cache()
+    if "sweeps" in ops:
+        by_op["sweeps"] = bench_sweeps(ss, sg, torch, stream)
 
     if rank != 0:
         if world > 1:

@@ -99,6 +99,13 @@ typedef struct {
  * partition.  Equal keys are contiguous and in input order, but groups are not
  * in key order (the semisort_equal contract). */
 #define SS_FLAG_HASH_BUCKETS 0x4
+/* semisort_equal / semisort_less (and their batched forms): one temporary
+ * array instead of two.  The distribution levels alternate between the
+ * temporary and the caller's output arrays -- the swap of A and T of Sec. 3.4
+ * -- so the workspace is about half as large (17.6 GB instead of 33.6 GB for
+ * 10^9 u64/u64 records).  Same results; the levels that write the output
+ * arrays write keys and values separately, which costs time. */
+#define SS_FLAG_SWAP_OUTPUT 0x8
 
 /* Bytes of workspace needed by `op` on n records with the given types and
  * options (NULL = defaults).  Returns SS_ERR_UNSUPPORTED for unsupported type
@@ -170,9 +177,12 @@ ss_status semisort_equal_noalloc(ss_type key_type, ss_type val_type, const void*
                                  const ss_options* opt, ss_stream_t stream);
 
 /* The learned-splitter model on its own.  semisort_less with
- * options.splitter_mode = 1 fits a monotone CDF model to its 2^16-key top-level
- * sample and inverts it into the top level's splitters (a gain in load
- * balance only: bucketing stays exact key comparison).  The model is a 1-32-32-1
+ * options.splitter_mode = 1 fits a monotone CDF model to the light (non-heavy)
+ * keys of its 2^16-key top-level sample and inverts it into the top level's
+ * splitters (a gain in load balance only: bucketing stays exact key
+ * comparison).  Heavy keys keep their own equality buckets.  Training runs
+ * every Adam step in one launch of a cluster of 8 CTAs and stops on a loss
+ * plateau.  The model is a 1-32-32-1
  * perceptron in FP32 with softplus-positive weights and logistic hidden units;
  * SS_MLP_PARAMS parameters laid out v1[32] | c1[32] | v2[32*32] (row j: the
  * weights into hidden unit j of layer 2) | c2[32] | v3[32] | c3, with weights
@@ -210,9 +220,15 @@ ss_status ss_mlp_invert(const float* d_params, ss_type key_type, uint64_t kmin, 
  * records go straight to the base case, larger ones become the top level's
  * segments, so one call enqueues the same fixed kernel sequence whatever the
  * instance sizes (and can be captured in a CUDA graph).  Workspace:
- * ss_workspace_size_batched().  options.splitter_mode is ignored (sampled
- * splitters); options.subarray also sets the top level's subarray size
- * (default 2^18 records). */
+ * ss_workspace_size_batched().  options.subarray also sets the top level's
+ * subarray size (default 2^18 records).  options.splitter_mode = 1 with
+ * semisort_less_batched and 32- or 64-bit keys: one CDF model is trained on a
+ * 2^16-key sample of the whole batch (light keys only) and inverted at 2^8
+ * ranges; every instance above alpha judges the model's splitters against
+ * those of its own sample (the model's are kept unless their largest range
+ * bucket exceeds twice the light keys' share and the sampled splitters'
+ * largest); ss_get_stats entry 12 counts the instances that kept them.
+ * Results are the same either way. */
 ss_status ss_workspace_size_batched(int op, ss_type key_type, ss_type val_type, uint64_t n,
                                     uint32_t num_instances, const ss_options* opt, size_t* bytes);
 
@@ -255,9 +271,12 @@ ss_status ss_last_device_error(void* ws, ss_stream_t stream, int* code);
  * at levels 1, 2, 3 and 4-6 (4 entries), records refined, records copied, heavy keys at
  * level 1, largest refined bucket, refine items, records whose bucket was all
  * distinct keys, splitters of the semisort_< top level (0 sampled, 1 learned,
- * 2 learned but rejected on the sample), the largest top-level range bucket's
- * count in the 2^16-key sample, the largest top-level light bucket in records.
- * Returns the number of entries written. */
+ * 2 learned but rejected on the sample or not usable), the largest top-level
+ * range bucket's count in the 2^16-key sample (batched learned mode: the
+ * instances that kept the model's splitters), the largest top-level light
+ * bucket in records, the semisort_< top level's n_L, and the Adam steps the
+ * learned-splitter training ran (it stops early on a loss plateau).
+ * Returns the number of entries written (at most 16). */
 int ss_get_stats(void* ws, ss_stream_t stream, uint64_t* out, int count);
 
 /* Per-kernel timings (milliseconds) of the last call made with

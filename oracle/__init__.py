@@ -185,6 +185,31 @@ def histogram_hash(keys):
     return _reduce(_load().ss_oracle_histogram_hash, keys, None)
 
 
+def collect_reduce_fold(keys, vals, op, identity):
+    """collect-reduce with a general monoid (op, identity) (Sec. 2.1): for
+    every distinct key, in first-occurrence order, op folded left to right
+    over the key's values in input order -- the order a stable grouping keeps
+    (Sec. 3.5), so op need not be commutative.  keys: as for group_by; vals:
+    a sequence of Python values; op: a Python function.  Returns (unique
+    keys, list of folded values).  Plain Python over the records: small n."""
+    keys = _c(keys)
+    n = keys.shape[0]
+    gk, gi = group_by(keys, np.arange(n, dtype=np.uint64))
+    flat = gk.reshape(n, -1)
+    uk, out = [], []
+    i = 0
+    while i < n:
+        j = i
+        acc = identity
+        while j < n and np.array_equal(flat[j], flat[i]):
+            acc = op(acc, vals[int(gi[j])])
+            j += 1
+        uk.append(gk[i])
+        out.append(acc)
+        i = j
+    return (np.array(uk, dtype=keys.dtype).reshape((-1,) + keys.shape[1:]) if uk else keys[:0].copy()), out
+
+
 def count_runs(keys) -> int:
     keys = _c(keys)
     return int(_load().ss_oracle_count_runs(_key_code(keys), keys.shape[0], _ptr(keys)))

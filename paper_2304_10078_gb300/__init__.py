@@ -23,6 +23,7 @@ OP_EQUAL, OP_LESS, OP_REDUCE, OP_HIST = 0, 1, 2, 3
 FLAG_PHASE_TIMING = 0x1
 FLAG_IDENTITY_HASH = 0x2
 FLAG_HASH_BUCKETS = 0x4
+FLAG_SWAP_OUTPUT = 0x8
 
 STATUS = {
     0: "ok", 1: "invalid argument", 2: "unsupported type or size", 3: "workspace too small",
@@ -32,7 +33,7 @@ STATUS = {
 
 STAT_NAMES = ["levels", "dist_l0", "dist_l1", "dist_l2", "dist_l3", "refined", "copied",
               "heavy_l0", "max_refine", "refine_items", "all_distinct", "l0_splitters", "l0_max_sample_range",
-              "l0_max_light_bucket"]
+              "l0_max_light_bucket", "l0_light_buckets", "learn_steps"]
 
 
 class SemisortError(RuntimeError):

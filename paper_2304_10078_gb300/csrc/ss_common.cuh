@@ -10,6 +10,18 @@
 
 #include "ss_plan.h"
 
+namespace semisort {
+// Traits of a user-defined key type for the C++ template entry points
+// (include/semisort.hpp).  Specialize with
+//   __device__ static uint64_t hash(const K&);           equal keys hash equally
+//   __device__ static bool equal(const K&, const K&);    an equivalence
+//   __device__ static bool less(const K&, const K&);     a strict weak order (semisort_<)
+// Sec. 2.1 asks the user of a semisort for exactly these: a hash function
+// family, an equality test and, for semisort_<, a comparison.
+template <class K>
+struct key_traits;
+}  // namespace semisort
+
 namespace ss {
 
 constexpr uint32_t kEmpty = 0xFFFFFFFFu;
@@ -31,12 +43,27 @@ struct alignas(16) k128 {
   uint64_t lo, hi;
 };
 
+// Key traits used by the kernels.  The built-in types are specialized below;
+// any other key type reads semisort::key_traits (its hash is mixed with the
+// level salt, and equality always compares whole keys, so hash collisions
+// never merge groups).  kIntegral: an unsigned integer of at most 8 bytes,
+// which the semisort_< kernels may also treat as a number (lookup tables,
+// interpolation buckets).
 template <class K>
-struct KeyT;
+struct KeyT {
+  static constexpr int kCode = -1;
+  static constexpr bool kIntegral = false;
+  __device__ __forceinline__ static uint64_t hash(const K& k, uint64_t salt, bool) {
+    return mix64(semisort::key_traits<K>::hash(k) ^ salt);
+  }
+  __device__ __forceinline__ static bool eq(const K& a, const K& b) { return semisort::key_traits<K>::equal(a, b); }
+  __device__ __forceinline__ static bool lt(const K& a, const K& b) { return semisort::key_traits<K>::less(a, b); }
+};
 
 template <>
 struct KeyT<uint32_t> {
   static constexpr int kCode = 0;
+  static constexpr bool kIntegral = true;
   __device__ __forceinline__ static uint64_t hash(uint32_t k, uint64_t salt, bool ident) {
     return ident ? (uint64_t)k << 32 : mix64((uint64_t)k ^ salt);
   }
@@ -47,6 +74,7 @@ struct KeyT<uint32_t> {
 template <>
 struct KeyT<uint64_t> {
   static constexpr int kCode = 1;
+  static constexpr bool kIntegral = true;
   __device__ __forceinline__ static uint64_t hash(uint64_t k, uint64_t salt, bool ident) {
     return ident ? k : mix64(k ^ salt);
   }
@@ -57,6 +85,7 @@ struct KeyT<uint64_t> {
 template <>
 struct KeyT<k128> {
   static constexpr int kCode = 2;
+  static constexpr bool kIntegral = false;
   __device__ __forceinline__ static uint64_t hash(k128 k, uint64_t salt, bool ident) {
     return ident ? k.hi : mix64(k.lo ^ mix64(k.hi ^ salt));
   }
@@ -65,6 +94,12 @@ struct KeyT<k128> {
     return a.hi < b.hi || (a.hi == b.hi && a.lo < b.lo);
   }
 };
+
+// Heavy-key capacity of a segment with 2^lbits light buckets: min(n_L, 512).
+__host__ __device__ __forceinline__ uint32_t hcap_of(uint32_t lbits) {
+  const uint32_t nl = 1u << lbits;
+  return nl < kMaxHeavy ? nl : kMaxHeavy;
+}
 
 // Light-bucket id: the top `bits` bits of the level hash (bits >= 1).
 __device__ __forceinline__ uint32_t light_bucket(uint64_t h, uint32_t bits) {
@@ -286,7 +321,9 @@ struct ValT<void> {
 // lbits bits (Sec. 3.1 takes the bucket from hash bits; a fresh multiplier
 // per level plays the role of the next hash function of the family).
 template <class K>
-__device__ __forceinline__ uint64_t fold_key(const K& k);
+__device__ __forceinline__ uint64_t fold_key(const K& k) {
+  return semisort::key_traits<K>::hash(k);
+}
 template <>
 __device__ __forceinline__ uint64_t fold_key<uint32_t>(const uint32_t& k) { return k; }
 template <>

@@ -42,11 +42,13 @@ __device__ __forceinline__ uint32_t ceil_log2_u32(uint32_t x) { return x <= 1 ? 
 // Buffers of one level (the launcher computes them).
 struct LevelBufs {
   const void* src_k;  // SoA keys (src_aos == 0) or AoS records (src_aos == 1)
-  const void* src_v;  // SoA values (level 0 only)
-  void* dst;          // AoS records: light buckets
+  const void* src_v;  // SoA values (src_aos == 0)
+  void* dst;          // light buckets: AoS records (dst_aos == 1) or SoA keys
+  void* dst_v;        // light buckets: SoA values (dst_aos == 0)
   void* hdst_k;       // heavy destination: SoA keys, or AoS records when hdst_aos
   void* hdst_v;
   uint32_t src_aos;
+  uint32_t dst_aos;
   uint32_t hdst_aos;
   uint32_t dst_id;   // Buf id of dst
   uint32_t hdst_id;  // Buf id of the heavy destination
@@ -63,10 +65,6 @@ __device__ __forceinline__ K load_key(const void* src, uint32_t aos, uint64_t i)
   return aos ? reinterpret_cast<const RecT<K, V>*>(src)[i].k : reinterpret_cast<const K*>(src)[i];
 }
 
-__host__ __device__ __forceinline__ uint32_t hcap_of(uint32_t lbits) {
-  const uint32_t nl = 1u << lbits;
-  return nl < kMaxHeavy ? nl : kMaxHeavy;
-}
 
 // Heavy-key capacity of a segment (a power of two): hash-bucket segments keep
 // n_L + capacity <= kMaxBuckets, range segments use hcap_of.
@@ -146,11 +144,12 @@ __device__ __forceinline__ uint32_t bucket_less_tab(const K& k, const K* bnd, co
 }
 
 // Whether the semisort_< top level uses the wide bucket space (2^16-key
-// sample, up to 2^11 ranges): for keys up to 8 bytes, whose wide distribute
-// buffers fit in shared memory.
+// sample, up to 2^12 ranges, a lookup table over the key range): for
+// unsigned integer keys of up to 8 bytes, whose wide distribute buffers fit in
+// shared memory.
 template <class K, int OP>
 struct TopWide {
-  static constexpr bool value = OP == kOpLess && sizeof(K) < 16;
+  static constexpr bool value = OP == kOpLess && KeyT<K>::kIntegral;
 };
 
 // Whether bucket b holds a single heavy key (final after distribution).
@@ -367,6 +366,30 @@ __global__ void __launch_bounds__(1024) k_plan(Work w, int level) {
 // the heavy keys into one sorted boundary list (equality buckets for heavy
 // keys, samplesort-style).
 // ----------------------------------------------------------------------------
+// Largest sample count a range bucket of the learned splitters may hold
+// before the sampled splitters replace them: twice the light keys' share of a
+// range, plus four standard deviations of a sample count of that size (with
+// 2^16 sample keys and 4096 ranges a range holds about 16 of them, and even
+// exact splitters show a largest count near 31 from counting noise alone).
+__device__ __forceinline__ uint32_t judge_limit(uint32_t share) {
+  const float t = 2.0f * (float)(share > 1 ? share : 1);
+  return (uint32_t)(t + 4.0f * sqrtf(t));
+}
+
+// First position of the sorted S[0, m) holding a key > k (upper) or >= k.
+template <class K>
+__device__ __forceinline__ uint32_t sorted_bound(const K* S, uint32_t m, const K& k, bool upper) {
+  uint32_t lo = 0, hi = m;
+  while (lo < hi) {
+    const uint32_t mid = (lo + hi) >> 1;
+    if (upper ? !KeyT<K>::lt(k, S[mid]) : KeyT<K>::lt(S[mid], k))
+      lo = mid + 1;
+    else
+      hi = mid;
+  }
+  return lo;
+}
+
 template <class K, class V, int OP>
 __global__ void __launch_bounds__(1024) k_sample(Work w, LevelBufs lb, uint32_t s_cap) {
   extern __shared__ __align__(16) unsigned char smem[];
@@ -436,40 +459,98 @@ __global__ void __launch_bounds__(1024) k_sample(Work w, LevelBufs lb, uint32_t 
     __syncthreads();
     uint16_t* ht = w.htab[lb.level] + 2ull * sg.bbase;
     if constexpr (OP == kOpLess) {
-      if (threadIdx.x == 0) {
-        // merge splitters S[j S_n / n_L] (deduplicated) with the heavy keys
-        const uint32_t nl = sg.nl;
-        K* bnd = reinterpret_cast<K*>(w.splitters[lb.level]) + sg.bbase;
-        uint32_t q = 0, j = 1, hi = 0;
-        bool have_last = false;
-        K last = S[0];
-        while (j < nl || hi < nh) {
-          K cand;
-          bool heavy;
-          if (j < nl && (hi >= nh || KeyT<K>::lt(S[(uint64_t)j * S_n / nl], hk[hi]))) {
-            cand = S[(uint64_t)j * S_n / nl];
-            heavy = false;
-            ++j;
-          } else if (j < nl && KeyT<K>::eq(S[(uint64_t)j * S_n / nl], hk[hi])) {
-            cand = hk[hi];
-            heavy = true;
-            ++j;
-            ++hi;
-          } else {
-            cand = hk[hi];
-            heavy = true;
-            ++hi;
+      const uint32_t nl = sg.nl;
+      K* bnd = reinterpret_cast<K*>(w.splitters[lb.level]) + sg.bbase;
+      // batched calls in learned mode: the shared CDF model's splitters for
+      // this instance (the inverted splitters at 2^8 ranges, every
+      // 2^(8 - lbits)-th of them), judged against the sampled ones below
+      const LearnState* L = nullptr;
+      if constexpr (KeyT<K>::kIntegral) {
+        if (lb.level == 0 && w.num_inst > 1 && w.splitter_mode == 1) L = reinterpret_cast<const LearnState*>(w.learn);
+      }
+      const bool model = L != nullptr && L->usable && sg.lbits <= kBatchLearnLog2;
+      auto cand = [&](uint32_t j, bool use_model) -> K {
+        if (use_model) return reinterpret_cast<const K*>(L->splitters)[(j << (kBatchLearnLog2 - sg.lbits)) - 1];
+        return S[(uint64_t)j * S_n / nl];
+      };
+      // merge the n_L - 1 candidate splitters (deduplicated) with the heavy
+      // keys into the sorted boundaries; returns their number (thread 0)
+      auto merge = [&](bool use_model) {
+        if (threadIdx.x == 0) {
+          uint32_t q = 0, j = 1, hi = 0;
+          bool have_last = false;
+          K last = S[0], prev = S[0];
+          while (j < nl || hi < nh) {
+            K cj = j < nl ? cand(j, use_model) : S[0];
+            if (use_model && j < nl && j > 1 && KeyT<K>::lt(cj, prev)) cj = prev;  // FP32 rounding: keep it sorted
+            K c;
+            bool heavy;
+            if (j < nl && (hi >= nh || KeyT<K>::lt(cj, hk[hi]))) {
+              c = cj;
+              heavy = false;
+              prev = cj;
+              ++j;
+            } else if (j < nl && KeyT<K>::eq(cj, hk[hi])) {
+              c = hk[hi];
+              heavy = true;
+              prev = cj;
+              ++j;
+              ++hi;
+            } else {
+              c = hk[hi];
+              heavy = true;
+              ++hi;
+            }
+            if (have_last && KeyT<K>::eq(c, last)) {
+              if (heavy) ht[q - 1] = 1;
+              continue;
+            }
+            bnd[q] = c;
+            ht[q] = heavy ? 1 : 0;
+            ++q;
+            last = c;
+            have_last = true;
           }
-          if (have_last && KeyT<K>::eq(cand, last)) {
-            if (heavy) ht[q - 1] = 1;
-            continue;
-          }
-          bnd[q] = cand;
-          ht[q] = heavy ? 1 : 0;
-          ++q;
-          last = cand;
-          have_last = true;
+          nh_sh = q;
         }
+        __syncthreads();
+        return nh_sh;
+      };
+      // the largest range bucket of the boundaries on this segment's sample
+      auto max_range = [&](uint32_t q) {
+        if (threadIdx.x == 0) tmp[32] = 0;
+        __syncthreads();
+        uint32_t mx = 0;
+        for (uint32_t u = threadIdx.x; u <= q; u += blockDim.x) {
+          const uint32_t lo = u == 0 ? 0u : sorted_bound<K>(S, S_n, bnd[u - 1], ht[u - 1] != 0);
+          const uint32_t hi = u == q ? S_n : sorted_bound<K>(S, S_n, bnd[u], false);
+          mx = hi > lo && hi - lo > mx ? hi - lo : mx;
+        }
+        atomicMax(&tmp[32], mx);
+        __syncthreads();
+        const uint32_t r = tmp[32];
+        __syncthreads();
+        return r;
+      };
+      uint32_t q = merge(false);
+      if (model) {
+        const uint32_t max_s = max_range(q);
+        // light sample keys: those not equal to a heavy key
+        if (threadIdx.x == 0) tmp[32] = 0;
+        __syncthreads();
+        for (uint32_t i = threadIdx.x; i < nh; i += blockDim.x)
+          atomicAdd(&tmp[32], sorted_bound<K>(S, S_n, hk[i], true) - sorted_bound<K>(S, S_n, hk[i], false));
+        __syncthreads();
+        const uint32_t heavy_n = tmp[32];
+        __syncthreads();
+        const uint32_t share = (S_n - heavy_n + nl - 1) / nl;
+        q = merge(true);
+        const uint32_t max_l = max_range(q);
+        const bool reject = max_l > judge_limit(share) && max_l > max_s;
+        if (reject) q = merge(false);
+        if (threadIdx.x == 0 && !reject) atomicAdd((unsigned long long*)&w.ctrl->stats[12], 1ull);
+      }
+      if (threadIdx.x == 0) {
         w.segs[lb.level][s].nh = q;
         w.segs[lb.level][s].nb = 2 * q + 1;
         if (lb.level == 0) w.ctrl->stats[7] = nh;
@@ -560,11 +641,15 @@ __global__ void __launch_bounds__(256) k_bigsample_merge(Work w) {
 // mode, the integer splitters inverted from the CDF model -- merged with the
 // heavy keys (keys whose sample run reaches the expected size of one range
 // bucket, at most min(n_L, 512) of them in key order) into one sorted list with
-// a flag per heavy key (equality buckets, as in k_sample).  Learned splitters
-// are judged on the sample: if any range bucket would hold more than twice its
-// share of the (non-heavy) sample, the sampled splitters are used instead.
-// stats[11]: 0 sampled, 1 learned, 2 learned rejected; stats[12]: the largest
-// range bucket's sample count.  One CTA.
+// a flag per heavy key (equality buckets, as in k_sample).  The sampled
+// splitters judge the learned ones on the sample through the largest range
+// bucket: the model is rejected (sampled splitters used) when its largest
+// range bucket holds more than twice the light (non-heavy) sample keys'
+// share of a range (plus the sample's counting noise, judge_limit) and more
+// than the sampled splitters' largest one.
+// stats[11]: 0 sampled, 1 learned, 2 learned rejected or not usable;
+// stats[12]: the largest range bucket's sample count; stats[14]: the top
+// level's n_L; stats[15]: Adam steps of the training.  One CTA.
 template <class K>
 __device__ __forceinline__ uint32_t sample_lower(const K* S, const K& k, bool upper) {
   uint32_t lo = 0, hi = kBigSample;
@@ -612,12 +697,21 @@ __global__ void __launch_bounds__(1024) k_less_split(Work w, const LearnState* L
     __syncthreads();
   }
   const uint32_t nh = nh_sh < hcap ? nh_sh : hcap;
-  for (int attempt = 0; attempt < 2; ++attempt) {
+  // Learned mode judges both splitter sets on the sample: the sampled ones
+  // first (their largest range bucket), then the learned ones, which are kept
+  // unless their largest range bucket exceeds twice the light keys' share of
+  // a range and also the sampled splitters' largest one; a rejected model
+  // means a third pass rebuilds the sampled boundaries.
+  const uint32_t share = (L != nullptr ? (L->light + nl - 1) / nl : kBigSample / nl);
+  const int passes = learned ? 3 : 1;
+  uint32_t max_sampled = 0;
+  for (int attempt = 0; attempt < passes; ++attempt) {
+    const bool use_model = learned && attempt == 1;
     for (uint32_t j = 1 + threadIdx.x; j < nl; j += blockDim.x)
-      cs[j - 1] = learned ? reinterpret_cast<const K*>(L->splitters)[j - 1] : S[(uint64_t)j * kBigSample / nl];
+      cs[j - 1] = use_model ? reinterpret_cast<const K*>(L->splitters)[j - 1] : S[(uint64_t)j * kBigSample / nl];
     __syncthreads();
     if (threadIdx.x == 0) {
-      if (learned)  // the bisection in FP32 may step back by a rounding: make the list non-decreasing
+      if (use_model)  // the bisection in FP32 may step back by a rounding: make the list non-decreasing
         for (uint32_t j = 1; j + 1 < nl; ++j)
           if (KeyT<K>::lt(cs[j], cs[j - 1])) cs[j] = cs[j - 1];
       // q <= (n_L - 1) + hcap < 2 n_L boundaries
@@ -663,10 +757,17 @@ __global__ void __launch_bounds__(1024) k_less_split(Work w, const LearnState* L
     }
     atomicMax(&maxc_sh, mx);
     __syncthreads();
-    const bool reject = learned && maxc_sh > 2 * (kBigSample / nl);
-    if (!reject) break;
-    learned = false;  // fall back to the sampled splitters
-    __syncthreads();
+    if (attempt == 0 && learned) {
+      max_sampled = maxc_sh;
+      __syncthreads();
+      continue;
+    }
+    if (attempt == 1) {
+      const bool reject = maxc_sh > judge_limit(share) && maxc_sh > max_sampled;
+      if (!reject) break;
+      learned = false;  // fall back to the sampled splitters (rebuilt by the third pass)
+      __syncthreads();
+    }
   }
   const uint32_t q = q_sh;
   K* bnd = reinterpret_cast<K*>(w.splitters[0]) + sgp[0].bbase;
@@ -711,6 +812,8 @@ __global__ void __launch_bounds__(1024) k_less_split(Work w, const LearnState* L
     w.ctrl->stats[7] = nh;
     w.ctrl->stats[11] = L == nullptr ? 0u : learned ? 1u : 2u;
     w.ctrl->stats[12] = maxc_sh;
+    w.ctrl->stats[14] = nl;
+    w.ctrl->stats[15] = L == nullptr ? 0u : L->steps_done;
   }
 }
 
@@ -1076,6 +1179,48 @@ __device__ __forceinline__ void load_chunk(RecT<K, V>* S, uint32_t len, Src src)
   }
 }
 
+
+// Hash-bucket ids of a thread's kDR records in one pass: every light bucket
+// first (no branches), then the first heavy-table probe of every record as
+// independent loads, then the rare longer probe chains.
+template <class K, class V>
+__device__ __forceinline__ void bucket_ids_hash(const RecT<K, V>* S, uint32_t c0t, uint32_t clen, const Seg& sg,
+                                                const K* hk, const uint16_t* ht, uint32_t tmask,
+                                                uint32_t (&bid)[kDR]) {
+  constexpr int RB = sizeof(RecT<K, V>);
+  K key[kDR];
+  uint32_t slot[kDR];
+  const bool ident = sg.ident != 0;
+#pragma unroll
+  for (int r = 0; r < kDR; ++r) {
+    key[r] = S[sw<RB>(c0t + r)].k;
+    const uint64_t f = fold_key<K>(key[r]);
+    const uint64_t h = f * sg.mult;
+    bid[r] = ident ? (sg.shift < 64 ? (uint32_t)(f >> sg.shift) & (sg.nl - 1) : 0u) : (uint32_t)__umul64hi(h, sg.nl);
+    slot[r] = (uint32_t)(h >> 20) & tmask;
+  }
+  if (sg.nh) {
+    uint32_t e[kDR];
+#pragma unroll
+    for (int r = 0; r < kDR; ++r) e[r] = ht[slot[r]];
+#pragma unroll
+    for (int r = 0; r < kDR; ++r) {
+      uint32_t s = slot[r], x = e[r];
+      while (x != 0xFFFFu) {
+        if (KeyT<K>::eq(hk[x], key[r])) {
+          bid[r] = sg.nl + x;
+          break;
+        }
+        s = (s + 1) & tmask;
+        x = ht[s];
+      }
+    }
+  }
+#pragma unroll
+  for (int r = 0; r < kDR; ++r)
+    if (c0t + r >= clen) bid[r] = 0x7FFFu;
+}
+
 // L2 prefetch of records [start, start + len) of a level's source (one
 // prefetch per 128-byte line, every address inside the range).
 template <class K, class V>
@@ -1191,14 +1336,18 @@ __global__ void __launch_bounds__(kDT, 2) k_distribute(Work w, LevelBufs lb) {
       uint32_t bid[kDR], rk[kDR];
       // invalid slots get id 2^15 - 1: every 5-bit digit is 31, and as the last
       // items in blocked order they rank after every valid record
+      if constexpr (OP != kOpLess && sizeof(K) <= 8) {
+        bucket_ids_hash<K, V>(sm.S, c0t, clen, sg, sm.hk, sm.ht, tmask, bid);
+      } else {
 #pragma unroll
-      for (int r = 0; r < kDR; ++r) {
-        if (c0t + r >= clen) {
-          bid[r] = 0x7FFFu;
-        } else if constexpr (BIG && OP == kOpLess) {
-          bid[r] = bucket_less_tab<K>(sm.S[sw<RB>(c0t + r)].k, sm.hk, sm.ht, sm.cell, tkmin, tshift);
-        } else {
-          bid[r] = bucket_in<K, OP>(sm.S[sw<RB>(c0t + r)].k, sg, sm.hk, sm.ht, tmask);
+        for (int r = 0; r < kDR; ++r) {
+          if (c0t + r >= clen) {
+            bid[r] = 0x7FFFu;
+          } else if constexpr (BIG) {
+            bid[r] = bucket_less_tab<K>(sm.S[sw<RB>(c0t + r)].k, sm.hk, sm.ht, sm.cell, tkmin, tshift);
+          } else {
+            bid[r] = bucket_in<K, OP>(sm.S[sw<RB>(c0t + r)].k, sg, sm.hk, sm.ht, tmask);
+          }
         }
       }
       DRank::rank(sm.rk, bid, 0, rk);
@@ -1271,7 +1420,12 @@ __global__ void __launch_bounds__(kDT, 2) k_distribute(Work w, LevelBufs lb) {
         const uint64_t pos = sg.start + sm.cur[b] + p;
         const Rec rec = sm.S[sw<RB>(x & 0xFFFFu)];
         if (!is_heavy<OP>(b, nl)) {
-          dst[pos] = rec;
+          if (lb.dst_aos) {
+            dst[pos] = rec;
+          } else {
+            reinterpret_cast<K*>(lb.dst)[pos] = rec.k;
+            if constexpr (kVals) reinterpret_cast<VV*>(lb.dst_v)[pos] = rec.v;
+          }
         } else if constexpr (kMoveHeavy) {
           if (lb.hdst_aos) {
             reinterpret_cast<Rec*>(lb.hdst_k)[pos] = rec;
@@ -1467,6 +1621,9 @@ __device__ __forceinline__ RecT<K, V> load_rec(const Work& w, uint32_t buf, uint
   if (buf == kBufIn) {
     r.k = reinterpret_cast<const K*>(w.in_k)[c];
     if constexpr (!std::is_same<V, void>::value) r.v = reinterpret_cast<const V*>(w.in_v)[c];
+  } else if (buf == kBufOut) {  // records a level left in the caller's output (Sec. 3.4)
+    r.k = reinterpret_cast<const K*>(w.out_k)[c];
+    if constexpr (!std::is_same<V, void>::value) r.v = reinterpret_cast<const V*>(w.out_v)[c];
   } else {
     r = reinterpret_cast<const RecT<K, V>*>(buf_ptr(w, buf))[c];
   }
@@ -1525,6 +1682,38 @@ __device__ __forceinline__ void rank_window(typename RRank::Smem& rs, uint32_t* 
   __syncthreads();
 }
 
+// L2 prefetch of a refine window's records.
+template <class K, class V>
+__device__ __forceinline__ void prefetch_item(const Work& w, const Item& it) {
+  auto pf = [&](const void* p0, uint64_t bytes) {
+    const char* p = reinterpret_cast<const char*>(p0);
+    const uint32_t lines = (uint32_t)((bytes + 127) / 128);
+    for (uint32_t l = threadIdx.x; l < lines; l += blockDim.x) {
+      uint64_t off = (uint64_t)l * 128;
+      if (off >= bytes) off = bytes - 1;
+      asm volatile("prefetch.global.L2 [%0];" ::"l"(p + off));
+    }
+  };
+  if (it.len == 0) return;
+  if (it.buf == kBufIn || it.buf == kBufOut) {
+    const void* kp = it.buf == kBufIn ? w.in_k : w.out_k;
+    const void* vp = it.buf == kBufIn ? w.in_v : w.out_v;
+    pf(reinterpret_cast<const K*>(kp) + it.start, (uint64_t)it.len * sizeof(K));
+    if constexpr (!std::is_same<V, void>::value)
+      pf(reinterpret_cast<const V*>(vp) + it.start, (uint64_t)it.len * sizeof(V));
+  } else {
+    pf(reinterpret_cast<const RecT<K, V>*>(buf_ptr(w, it.buf)) + it.start, (uint64_t)it.len * sizeof(RecT<K, V>));
+  }
+}
+
+// The refine window that follows item x in a CTA's sequence, if it is a
+// base case (copy items are not prefetched).
+__device__ __forceinline__ bool next_window(const Work& w, uint32_t x, uint32_t nfin, Item* out) {
+  if (x >= nfin) return false;
+  *out = w.items[x];
+  return out->kind == kItemRefine && out->len <= (uint32_t)kRefMax;
+}
+
 template <class K, class V>
 __global__ void __launch_bounds__(kRT, 2) k_finish_equal(Work w) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
@@ -1547,10 +1736,14 @@ __global__ void __launch_bounds__(kRT, 2) k_finish_equal(Work w) {
       if (tid == 0) set_error(w.ctrl, 8);
       continue;
     }
+    Item nx;
+    if (next_window(w, itx + gridDim.x, nfin, &nx)) prefetch_item<K, V>(w, nx);
     uint32_t ts = 64;
     while (ts < 2 * m) ts <<= 1;
-    auto ld = [&](uint32_t i) { return load_rec<K, V>(w, it.buf, it.start + i); };
-    load_chunk<kRT, K, V, decltype(ld), 16, 4>(sm.S, m, ld);
+    {
+      auto ld = [&](uint32_t i) { return load_rec<K, V>(w, it.buf, it.start + i); };
+      load_chunk<kRT, K, V, decltype(ld), 16, 4>(sm.S, m, ld);
+    }
     for (uint32_t i = tid; i < ts; i += kRT) sm.u.table[i] = kEmpty;
     __syncthreads();
     // the table slot of every record is parked in px until the labels are read
@@ -1635,7 +1828,7 @@ __global__ void __launch_bounds__(kRT, 2) k_finish_equal(Work w) {
 // ordered by bucket with input order inside each bucket, and an insertion sort
 // (stable) finishes every run of equal buckets.  Runs are short unless keys
 // repeat (then they are already in order) or cluster; a window with a long
-// unordered run -- and every window of 128-bit keys -- is sorted instead by
+// unordered run -- and every window of 128-bit or user-defined keys -- is sorted instead by
 // Batcher's bitonic network on (key, position in the window).  Either way the
 // output is the stable sort of the window.
 // ----------------------------------------------------------------------------
@@ -1673,16 +1866,20 @@ __global__ void __launch_bounds__(kRT, 2) k_finish_less(Work w) {
       if (tid == 0) set_error(w.ctrl, 8);
       continue;
     }
+    {
+      Item nx;  // the next window streams into L2 while this one is sorted
+      if (next_window(w, itx + gridDim.x, nfin, &nx)) prefetch_item<K, V>(w, nx);
+    }
     auto ld = [&](uint32_t i) { return load_rec<K, V>(w, it.buf, it.start + i); };
     load_chunk<kRT, K, V, decltype(ld), 16, 4>(sm.S, m, ld);
     if (tid == 0) {
-      sm.fallback = sizeof(K) > 8 ? 1u : 0u;
+      sm.fallback = KeyT<K>::kIntegral ? 0u : 1u;
       atomicAdd((unsigned long long*)&w.ctrl->stats[5], (unsigned long long)m);
       atomicAdd((unsigned long long*)&w.ctrl->stats[9], 1ull);
       atomicMax((unsigned long long*)&w.ctrl->stats[8], (unsigned long long)m);
     }
     __syncthreads();
-    if constexpr (sizeof(K) <= 8) {
+    if constexpr (KeyT<K>::kIntegral) {
       // key range of the window
       unsigned long long lo = ~0ull, hi = 0;
 #pragma unroll
@@ -1874,6 +2071,10 @@ __global__ void __launch_bounds__(kRT, 2) k_finish_reduce(Work w) {
         w.item_out[itx] = 0;
       }
       continue;
+    }
+    {
+      Item nx;  // the next window streams into L2 while this one is reduced
+      if (next_window(w, itx + gridDim.x, nfin, &nx)) prefetch_item<K, V>(w, nx);
     }
     uint32_t ts = 64;
     while (ts < 2 * m) ts <<= 1;

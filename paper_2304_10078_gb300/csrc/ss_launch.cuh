@@ -32,33 +32,53 @@ static cudaError_t set_smem(F* f, size_t bytes) {
 }
 
 // Buffer roles.  Level 0 reads the caller's input (structure of arrays) and
-// writes light records to T; level l >= 1 reads T or T2 (records) and writes
-// the other one, so records move once per level (the swap of Sec. 3.4).
-// Heavy records go straight to the output whenever the output is not being
-// read at that level; otherwise (in-place level 0) they stay in T and a copy
-// item moves them later.  collect-reduce / histogram never move heavy records.
+// writes light records to the temporary T (array of structures); level
+// l >= 1 reads T or T2 and writes the other one, so records move once per
+// level.  With SS_FLAG_SWAP_OUTPUT (semisort_= and semisort_< only) T2 is not
+// used: odd levels read T and write the caller's output arrays (structure of
+// arrays), even levels >= 2 read the output and write T -- the swap of A and
+// T of Sec. 3.4.  Heavy records go straight to the output whenever the output
+// is not being read at that level; otherwise (in-place level 0, even levels
+// >= 2 of the swap) they stay in T and a copy item moves them later.
+// collect-reduce / histogram never move heavy records.
 template <int OP>
 static LevelBufs level_bufs(const Work& w, int level) {
+  constexpr bool kSemi = OP == kOpEqual || OP == kOpLess;
   LevelBufs b;
   b.level = level;
-  const uint32_t src_id = level == 0 ? (uint32_t)kBufIn : (level % 2 == 1 ? (uint32_t)kBufT : (uint32_t)kBufT2);
-  const uint32_t dst_id = level % 2 == 0 ? (uint32_t)kBufT : (uint32_t)kBufT2;
-  b.src_k = level == 0 ? w.in_k : (src_id == kBufT ? w.t_k : w.t2_k);
-  b.src_v = level == 0 ? w.in_v : nullptr;
-  b.src_aos = level == 0 ? 0u : 1u;
-  b.dst = dst_id == kBufT ? w.t_k : w.t2_k;
+  uint32_t src_id, dst_id;
+  if (kSemi && w.swap) {
+    src_id = level == 0 ? (uint32_t)kBufIn : (level % 2 == 1 ? (uint32_t)kBufT : (uint32_t)kBufOut);
+    dst_id = level % 2 == 0 ? (uint32_t)kBufT : (uint32_t)kBufOut;
+  } else {
+    src_id = level == 0 ? (uint32_t)kBufIn : (level % 2 == 1 ? (uint32_t)kBufT : (uint32_t)kBufT2);
+    dst_id = level % 2 == 0 ? (uint32_t)kBufT : (uint32_t)kBufT2;
+  }
+  auto ptr = [&](uint32_t id) -> void* {
+    return id == kBufIn ? const_cast<void*>(w.in_k) : id == kBufT ? w.t_k : id == kBufOut ? w.out_k : w.t2_k;
+  };
+  const bool soa_src = src_id == kBufIn || src_id == kBufOut;
+  b.src_k = ptr(src_id);
+  b.src_v = src_id == kBufIn ? w.in_v : src_id == kBufOut ? w.out_v : nullptr;
+  b.src_aos = soa_src ? 0u : 1u;
+  b.dst = ptr(dst_id);
+  b.dst_v = dst_id == kBufOut ? w.out_v : nullptr;
+  b.dst_aos = dst_id == kBufOut ? 0u : 1u;
   b.dst_id = dst_id;
-  const bool out_is_read = level == 0 && w.in_k == w.out_k;
-  if ((OP == kOpEqual || OP == kOpLess) && !out_is_read) {
+  const bool out_is_read = src_id == kBufOut || (src_id == kBufIn && w.in_k == w.out_k);
+  if (kSemi && !out_is_read) {
     b.hdst_k = w.out_k;
     b.hdst_v = w.out_v;
     b.hdst_aos = 0;
     b.hdst_id = kBufOut;
   } else {
-    b.hdst_k = b.dst;
+    // heavy records into the level's AoS destination: T for semisort (the
+    // output is being read), the level's temporary for collect-reduce
+    const uint32_t hid = kSemi ? (uint32_t)kBufT : dst_id;
+    b.hdst_k = ptr(hid);
     b.hdst_v = nullptr;
     b.hdst_aos = 1;
-    b.hdst_id = dst_id;
+    b.hdst_id = hid;
   }
   return b;
 }
@@ -85,6 +105,7 @@ cudaError_t launch_pipeline(const Plan& P, const Work& w, cudaStream_t st, const
   const size_t bigs_smem = (size_t)BigRun<K>::len * sizeof(K);
   const size_t split_smem = less_split_smem<K>();
   if constexpr (kWide) {
+    if ((e = set_smem(k_learn_train, sizeof(TrainSmem))) != cudaSuccess) return e;
     if ((e = set_smem(k_bigsample_sort<K>, bigs_smem)) != cudaSuccess) return e;
     if ((e = set_smem(k_less_split<K>, split_smem)) != cudaSuccess) return e;
   }
@@ -124,17 +145,33 @@ cudaError_t launch_pipeline(const Plan& P, const Work& w, cudaStream_t st, const
         if (w.splitter_mode == 1) {
           // learned splitters: fit the CDF model to the sorted sample, invert it
           ls = reinterpret_cast<LearnState*>(w.learn);
-          k_learn_prep<K><<<1, 1024, 0, st>>>(reinterpret_cast<const K*>(w.bigs), ls, w.seed);
-          for (int s = 1; s <= kLearnSteps; ++s)
-            k_learn_step<<<kLearnPts / kGradPts, kGradThreads, 0, st>>>(ls, s, kLearnLr);
+          k_learn_prep<K><<<1, 1024, 0, st>>>(reinterpret_cast<const K*>(w.bigs), ls, w.seed, w.segs[0],
+                                              reinterpret_cast<K*>(w.bigs_tmp), 0u);
+          // every Adam step in one launch of one thread-block cluster
+          k_learn_train<<<kTrainCTAs, kTrainThreads, sizeof(TrainSmem), st>>>(ls, kLearnSteps, kLearnLr, 1);
           k_learn_invert<K><<<((1u << kLessTopLog2) + 255) / 256, 256, 0, st>>>(ls, w.segs[0], 0);
-          nl += kLearnSteps + 2;
+          nl += 3;
           if (tm) tm->mark("learn.L0");
         }
         k_less_split<K><<<1, 1024, split_smem, st>>>(w, ls);
         ++nl;
         }
       } else {
+        if constexpr (kWide) {
+          if (level == 0 && w.num_inst > 1 && w.splitter_mode == 1) {
+            // batched learned mode: one model from a sample of the whole batch,
+            // inverted at 2^8 ranges; k_sample judges it per instance
+            LearnState* ls = reinterpret_cast<LearnState*>(w.learn);
+            k_bigsample_sort<K><<<BigRun<K>::runs, 1024, bigs_smem, st>>>(w);
+            k_bigsample_merge<K><<<kBigSample / 256, 256, 0, st>>>(w);
+            k_learn_prep<K><<<1, 1024, 0, st>>>(reinterpret_cast<const K*>(w.bigs), ls, w.seed, nullptr,
+                                                reinterpret_cast<K*>(w.bigs_tmp), (uint32_t)kBatchLearnLog2);
+            k_learn_train<<<kTrainCTAs, kTrainThreads, sizeof(TrainSmem), st>>>(ls, kLearnSteps, kLearnLr, 1);
+            k_learn_invert<K><<<((1u << kBatchLearnLog2) + 255) / 256, 256, 0, st>>>(ls, nullptr, kBatchLearnLog2);
+            nl += 5;
+            if (tm) tm->mark("learn.L0");
+          }
+        }
         const uint32_t s_cap = level == 0 ? P.s1 : P.s2;
         k_sample<K, V, OP><<<cap(segs, nsm * 2), 1024, (size_t)s_cap * sizeof(K), st>>>(w, lb, s_cap);
         ++nl;

@@ -16,13 +16,18 @@ constexpr int kMaxLightLog2 = 9;       // n_L <= 512 per segment
 constexpr uint32_t kMaxHeavy = 512;    // heavy keys per segment
 constexpr uint32_t kMaxBuckets = 1024; // n_L + heavy: bucket ids fit two 5-bit rank passes
 constexpr uint32_t kCopyChunk = 1u << 16;  // records per copy item
-// semisort_< top level: up to 2^11 key ranges cut from a 2^16-key sample; with
-// up to 512 heavy equality buckets the 2q + 1 bucket ids stay below 2^13 and
-// are ranked in three 5-bit passes.
-constexpr int kLessTopLog2 = 11;
-constexpr uint32_t kBigBuckets = 8192;
+// semisort_< top level: up to 2^12 key ranges (4095 splitters) cut from a
+// 2^16-key sample; with up to 512 heavy equality buckets the q < 4608
+// boundaries give 2q + 1 < 9217 bucket ids, ranked in three 5-bit passes.
+constexpr int kLessTopLog2 = 12;
 constexpr uint32_t kBigBounds = (1u << kLessTopLog2) + kMaxHeavy;
+constexpr uint32_t kBigBuckets = 2 * kBigBounds + 16;
 constexpr uint32_t kBigSample = 1u << 16;
+// Batched semisort_< in learned mode: one CDF model for all instances, trained
+// on a 2^16-key sample of the whole batch and inverted at 2^8 ranges (the
+// largest range count of a narrow level); an instance with 2^l ranges takes
+// every 2^(8 - l)-th splitter.
+constexpr int kBatchLearnLog2 = 8;
 
 // Operations.
 enum Op : int { kOpEqual = 0, kOpLess = 1, kOpReduce = 2, kOpHist = 3 };
@@ -112,6 +117,7 @@ struct Work {
   uint32_t op;
   uint32_t ident;      // identity hash for integer keys (bucket ids from the key's own bits)
   uint32_t less_base;  // semisort_< with hash buckets: sort each base case
+  uint32_t swap;       // semisort: levels alternate between T and the output arrays (no T2)
   uint32_t auto_nl;    // top-level n_L chosen by size (no n_light_log2 option)
   uint32_t out_cap;    // collect-reduce / histogram capacity (clamped)
   uint64_t seed;

@@ -138,3 +138,35 @@ def test_graph_capture_replay(ss):
         torch.cuda.synchronize()
         assert np.array_equal(to_host(ko), want_k) and np.array_equal(to_host(vo), want_v)
     check_semisort("equal", off, keys, vals, want_k, want_v)
+
+
+@pytest.mark.parametrize("kt", ["u64", "u32"])
+def test_semisort_less_batched_learned(ss, kt):
+    """Batched semisort_< in learned mode: one model trained on a sample of
+    the whole batch, judged per instance; every instance's output is still
+    its stable sort, and instances with a smooth key distribution keep the
+    model's splitters (statistics entry 12)."""
+    import torch
+    ni = 40
+    sizes = np.floor(2.0 ** (14 + 6 * synth.unit(synth.rand64(0x1EA5, 0x1A, np.arange(ni, dtype=np.uint64)))))
+    sizes = sizes.astype(np.int64)
+    off = np.concatenate([[0], np.cumsum(sizes)]).astype(np.uint64)
+    n = int(off[-1])
+    # R-MAT-like skew: a Zipf head over a smooth exponential body, same law in every instance
+    keys = np.where(synth.uniform_mod(0x1EA6, n, 4) == 0, synth.zipf(0x1EA7, n, 1.2, N=10**6),
+                    synth.exponential(0x1EA8, n, 1e-7)).astype(np.uint64)
+    if kt == "u32":
+        keys = (keys & np.uint64(0xFFFFFFFF)).astype(np.uint32)
+    vals = np.arange(n, dtype=np.uint64)
+    k, v, o = to_dev(keys), to_dev(vals), to_dev(off)
+    res = {}
+    for mode in (0, 1):
+        opt = ss.make_options(seed=2, splitter_mode=mode)
+        ws = ss.alloc_workspace_batched(ss.OP_LESS, k, o, v, opt)
+        ko, vo = ss.semisort_less_batched(k, v, o, workspace=ws, options=opt)
+        torch.cuda.synchronize()
+        assert ss.last_device_error(ws) == 0
+        res[mode] = (to_host(ko), to_host(vo), ss.stats(ws))
+    check_semisort("less", off, keys, vals, res[1][0], res[1][1])
+    assert np.array_equal(res[0][0], res[1][0]) and np.array_equal(res[0][1], res[1][1])
+    assert res[1][2]["l0_max_sample_range"] > 0, res[1][2]  # instances that kept the model's splitters

@@ -162,6 +162,37 @@ def test_learned_gain_in_top_level_balance(ss):
     _, _, st_s = run_less(ss, keys, vals, 0)
     _, _, st_l = run_less(ss, keys, vals, 1)
     assert st_s["l0_splitters"] == 0 and st_l["l0_splitters"] == 1
-    mean = n / 2048
+    mean = n / st_s["l0_light_buckets"]
     ratio_s, ratio_l = st_s["l0_max_light_bucket"] / mean, st_l["l0_max_light_bucket"] / mean
     assert ratio_l < ratio_s, (ratio_l, ratio_s)
+
+
+@pytest.mark.parametrize("kind", ["uniform", "zipf12", "exponential", "gaussian_mixture"])
+def test_learned_judged_against_sampled(ss, kind):
+    """The sampled splitters judge the model on the 2^16-key sample: the
+    learned splitters are kept unless their largest range bucket exceeds twice
+    a range's share of the light keys (plus four standard deviations of
+    counting noise) and also the sampled splitters' largest one; a rejected
+    model leaves exactly the sampled partition.  Either way the
+    output is the stable sort; the training stops within its step budget."""
+    n = 1 << 24
+    keys = {"uniform": lambda: synth.uniform_exact(94, n, n),
+            "zipf12": lambda: synth.zipf(91, n, 1.2),
+            "exponential": lambda: synth.exponential(92, n, 1e-6),
+            "gaussian_mixture": lambda: synth.gaussian_mixture(93, n)}[kind]()
+    vals = np.arange(n, dtype=np.uint64)
+    _, _, st_s = run_less(ss, keys, vals, 0)
+    ko, vo, st_l = run_less(ss, keys, vals, 1)
+    assert st_s["l0_splitters"] == 0 and st_l["l0_splitters"] in (1, 2)
+    assert 0 < st_l["learn_steps"] <= 400
+    share_max = -(-65536 // st_s["l0_light_buckets"])
+    limit = int(2 * share_max + 4 * np.sqrt(2 * share_max))  # twice the share plus counting noise
+    if st_l["l0_splitters"] == 1:
+        assert st_l["l0_max_sample_range"] <= max(limit, st_s["l0_max_sample_range"]), (st_l, st_s)
+    else:
+        assert st_l["l0_max_sample_range"] == st_s["l0_max_sample_range"]
+        assert st_l["l0_max_light_bucket"] == st_s["l0_max_light_bucket"]
+    if kind == "uniform":
+        assert st_l["l0_splitters"] == 1  # smooth keys: the model beats the sample's quantile noise
+    err = oracle.check_sorted_equal(keys, vals, ko, vo)
+    assert err is None, err

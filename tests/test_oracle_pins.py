@@ -284,3 +284,24 @@ def test_parallel_stable_sort_equals_serial_and_numpy(kt, vt, threads):
     assert np.array_equal(pk, sk) and np.array_equal(pv, sv)
     order = np.argsort(keys, kind="stable")
     assert np.array_equal(pk, keys[order]) and np.array_equal(pv, vals[order])
+
+
+def test_collect_reduce_fold_pins():
+    """The general-monoid oracle: with (+ mod 2^64, 0) it equals the hash
+    collect-reduce; with a non-commutative op (tuple concatenation) every
+    key's fold is its values in input order, checked by brute force."""
+    rng = np.random.default_rng(33)
+    keys = rng.integers(0, 50, size=3000).astype(np.uint64)
+    vals = [int(x) for x in rng.integers(0, 2**63, size=3000)]
+    uk, out = oracle.collect_reduce_fold(keys, vals, lambda a, b: (a + b) % 2**64, 0)
+    hk, hs = oracle.collect_reduce_hash(keys, np.array(vals, dtype=np.uint64))
+    assert np.array_equal(uk, hk) and [int(x) for x in hs] == out
+    uk, out = oracle.collect_reduce_fold(keys, list(range(3000)), lambda a, b: a + (b,), ())
+    first = {}
+    for i, k in enumerate(keys.tolist()):
+        first.setdefault(k, []).append(i)
+    assert [int(k) for k in uk] == list(first.keys())
+    assert out == [tuple(v) for v in first.values()]
+    k2 = np.stack([keys, keys * 3], axis=1).astype(np.uint64)  # 128-bit keys
+    uk2, out2 = oracle.collect_reduce_fold(k2, list(range(3000)), lambda a, b: a + (b,), ())
+    assert np.array_equal(uk2[:, 0], uk) and out2 == out
