@@ -144,17 +144,17 @@ def test_graph_capture_replay(ss):
 def test_semisort_less_batched_learned(ss, kt):
     """Batched semisort_< in learned mode: one model trained on a sample of
     the whole batch, judged per instance; every instance's output is still
-    its stable sort, and instances with a smooth key distribution keep the
-    model's splitters (statistics entry 12)."""
+    its stable sort, and with smooth light keys the instances keep the model's
+    splitters (statistics entry 12)."""
     import torch
     ni = 40
     sizes = np.floor(2.0 ** (14 + 6 * synth.unit(synth.rand64(0x1EA5, 0x1A, np.arange(ni, dtype=np.uint64)))))
     sizes = sizes.astype(np.int64)
     off = np.concatenate([[0], np.cumsum(sizes)]).astype(np.uint64)
     n = int(off[-1])
-    # R-MAT-like skew: a Zipf head over a smooth exponential body, same law in every instance
+    # a Zipf head (heavy keys, equality buckets) over smooth light keys, same law in every instance
     keys = np.where(synth.uniform_mod(0x1EA6, n, 4) == 0, synth.zipf(0x1EA7, n, 1.2, N=10**6),
-                    synth.exponential(0x1EA8, n, 1e-7)).astype(np.uint64)
+                    synth.splitmix64_outputs(0x1EA8, n)).astype(np.uint64)
     if kt == "u32":
         keys = (keys & np.uint64(0xFFFFFFFF)).astype(np.uint32)
     vals = np.arange(n, dtype=np.uint64)
