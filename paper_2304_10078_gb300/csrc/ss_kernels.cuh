@@ -1589,9 +1589,9 @@ __global__ void __launch_bounds__(1024) k_emit(Work w, LevelBufs lb) {
 // the temporary array.
 //
 // Base case: the window's records are copied once, coalesced, into a swizzled
-// shared buffer.  A shared-memory hash table maps each key to the index of its
-// first occurrence in the window (insert by atomicCAS, then atomicMin, so the
-// label does not depend on scheduling).  A scan over first occurrences turns
+// shared buffer.  Rounds of minimum reductions into a shared-memory hash table
+// give every record the index of its key's first occurrence in the window
+// (first_occurrences; the label does not depend on scheduling).  A scan over first occurrences turns
 // labels into group ids 0..G-1 in first-occurrence order; ranking the records
 // stably by group id (BlockRank, ceil(log2 G)/5 passes) puts every group in one
 // run, groups in first-occurrence order and records of a group in input order
@@ -1602,6 +1602,57 @@ constexpr int kRT = 256;
 constexpr int kRR = 16;
 constexpr int kRefMax = kRT * kRR;  // alpha upper bound (4096)
 using RRank = BlockRank<kRT, kRR, 5>;
+
+// First occurrences in a base-case window (the grouping step of the semisort_=
+// and collect-reduce base cases, Sec. 3.3 and Sec. 3.5): for every record c
+// of the window the smallest index o with key(o) == key(c).
+//
+// Rounds of minimum reductions into a shared-memory table of 2^tbits words
+// (all kEmpty on entry, left dirty): in round k every record without a label
+// reduces (tag_k << 12 | c) into the slot of its key under the round's hash;
+// after a barrier the slot holds the smallest index o among the records that
+// met there.  All records of one key meet in the same slot, so a record whose
+// key equals key(o) takes o as its label (its key's first occurrence); the
+// others move on to the next round's hash.  Tags fall from round to round, so
+// values a slot kept from earlier rounds lose every minimum and the table is
+// never cleared.  Every round settles at least the key of each slot used, so
+// the rounds end.  No record waits on another record's result inside a
+// round, which keeps the shared-memory atomics pipelined.
+//
+// Records are held kRR per thread in blocked order (c = c0t + r).  keyat(c)
+// reads the key of record c; lab(r, o) receives the label of each valid
+// record.  Contains barriers: every thread of the block calls it.
+__device__ __forceinline__ uint64_t round_mult(uint64_t salt, uint32_t round) {
+  return (salt | 1) * (0x9E3779B97F4A7C15ull * (2ull * round + 1) | 1);
+}
+template <class K, class KeyAt, class Lab>
+__device__ __forceinline__ void first_occurrences(uint32_t* table, uint32_t tbits, uint32_t m, uint32_t c0t,
+                                                  uint64_t salt, KeyAt keyat, Lab lab) {
+  auto slot = [&](const K& key, uint64_t mul) { return (uint32_t)((fold_key<K>(key) * mul) >> (64 - tbits)); };
+  uint32_t pend = 0;  // bit r: record c0t + r has no label yet
+#pragma unroll
+  for (int r = 0; r < kRR; ++r) pend |= (c0t + r < m) ? 1u << r : 0u;
+  for (uint32_t round = 0;; ++round) {
+    const uint64_t mul = round_mult(salt, round);
+    const uint32_t tag = (0xFFFFEu - round) << 12;  // below kEmpty for every round and index
+#pragma unroll
+    for (int r = 0; r < kRR; ++r)
+      if (pend >> r & 1u) atomicMin(&table[slot(keyat(c0t + r), mul)], tag | (c0t + r));
+    __syncthreads();
+#pragma unroll
+    for (int r = 0; r < kRR; ++r) {
+      if (pend >> r & 1u) {
+        const K key = keyat(c0t + r);
+        const uint32_t o = table[slot(key, mul)] & 0xFFFu;
+        if (KeyT<K>::eq(keyat(o), key)) {
+          lab(r, o);
+          pend &= ~(1u << r);
+        }
+      }
+    }
+    if (!__syncthreads_or(pend != 0)) break;
+  }
+}
 
 template <class K, class V>
 struct RefSmem {
@@ -1746,41 +1797,16 @@ __global__ void __launch_bounds__(kRT, 2) k_finish_equal(Work w) {
     }
     for (uint32_t i = tid; i < ts; i += kRT) sm.u.table[i] = kEmpty;
     __syncthreads();
-    // the table slot of every record is parked in px until the labels are read
-#pragma unroll
-    for (int r = 0; r < kRR; ++r) {
-      const uint32_t c = c0t + r;
-      uint32_t s = 0;
-      if (c < m) {
-        const K key = sm.S[sw<RB>(c)].k;
-        // multiply-shift with the refine salt (bits independent of the bucketing)
-        const uint64_t h = fold_key<K>(key) * (salt | 1);
-        s = (uint32_t)(h >> 40) & (ts - 1);
-        while (true) {
-          uint32_t e = sm.u.table[s];
-          if (e == kEmpty) {
-            e = atomicCAS(&sm.u.table[s], kEmpty, c);
-            if (e == kEmpty) break;
-          }
-          if (KeyT<K>::eq(sm.S[sw<RB>(e)].k, key)) {
-            atomicMin(&sm.u.table[s], c);
-            break;
-          }
-          s = (s + 1) & (ts - 1);
-        }
-      }
-      sm.px[bpad(c)] = s;
-    }
-    __syncthreads();
-    // first-occurrence labels (kept per record in px) -> group ids in
-    // first-occurrence order (kept per first occurrence in the table region)
+    first_occurrences<K>(sm.u.table, 31 - __clz(ts), m, c0t, salt,
+                         [&](uint32_t i) { return sm.S[sw<RB>(i)].k; },
+                         [&](int r, uint32_t o) { sm.px[bpad(c0t + r)] = o; });
+    // labels (first occurrences, in px) -> group ids in first-occurrence
+    // order (kept per first occurrence in the table region)
     uint32_t nfirst = 0;
 #pragma unroll
     for (int r = 0; r < kRR; ++r) {
       const uint32_t c = c0t + r;
-      const uint32_t lab = c < m ? sm.u.table[sm.px[bpad(c)]] : 0;
-      sm.px[bpad(c)] = lab;
-      nfirst += (c < m && lab == c) ? 1u : 0u;
+      nfirst += (c < m && sm.px[bpad(c)] == c) ? 1u : 0u;
     }
     uint32_t G;
     uint32_t g0 = block_exclusive_scan(nfirst, sm.scan_tmp, &G);  // its barriers end the table reads
@@ -2007,8 +2033,8 @@ __global__ void __launch_bounds__(kRT, 2) k_finish_less(Work w) {
 
 // ----------------------------------------------------------------------------
 // finish (collect-reduce, histogram; Sec. 3.5).  Refine windows: a shared-
-// memory hash table finds each key's first occurrence (atomicCAS, then
-// atomicMin, as in the semisort_= base case); first occurrences numbered in
+// memory hash table finds each key's first occurrence (first_occurrences, as
+// in the semisort_= base case); first occurrences numbered in
 // window order give group ids, and the values (collect-reduce) or ones
 // (histogram) are added per group.  The G distinct (key, sum) pairs are
 // written compacted over the window's own first G slots (its records are no
@@ -2083,36 +2109,15 @@ __global__ void __launch_bounds__(kRT, 2) k_finish_reduce(Work w) {
                                     : reinterpret_cast<const Rec*>(buf_ptr(w, it.buf))[it.start + c].k;
     for (uint32_t i = tid; i < ts; i += kRT) sm.table[i] = kEmpty;
     __syncthreads();
-    uint32_t slot[kRR];
-#pragma unroll
-    for (int r = 0; r < kRR; ++r) {
-      const uint32_t c = c0t + r;
-      slot[r] = 0;
-      if (c < m) {
-        const K key = sm.keys[c];
-        uint32_t s = (uint32_t)KeyT<K>::hash(key, salt, false) & (ts - 1);
-        while (true) {
-          uint32_t e = sm.table[s];
-          if (e == kEmpty) {
-            e = atomicCAS(&sm.table[s], kEmpty, c);
-            if (e == kEmpty) break;
-          }
-          if (KeyT<K>::eq(sm.keys[e], key)) {
-            atomicMin(&sm.table[s], c);
-            break;
-          }
-          s = (s + 1) & (ts - 1);
-        }
-        slot[r] = s;
-      }
-    }
-    __syncthreads();
     uint32_t lab[kRR];
+#pragma unroll
+    for (int r = 0; r < kRR; ++r) lab[r] = 0;
+    first_occurrences<K>(sm.table, 31 - __clz(ts), m, c0t, salt, [&](uint32_t i) { return sm.keys[i]; },
+                         [&](int r, uint32_t o) { lab[r] = o; });
     uint32_t nfirst = 0;
 #pragma unroll
     for (int r = 0; r < kRR; ++r) {
       const uint32_t c = c0t + r;
-      lab[r] = c < m ? sm.table[slot[r]] : 0;
       nfirst += (c < m && lab[r] == c) ? 1u : 0u;
     }
     uint32_t G;
