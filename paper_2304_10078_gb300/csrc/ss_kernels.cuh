@@ -143,6 +143,28 @@ __device__ __forceinline__ uint32_t bucket_less_tab(const K& k, const K* bnd, co
   return 2 * lo;
 }
 
+// The same search through a narrow level's key-cell table: 2^cbits cells
+// over [kmin, kmin + 2^(shift + cbits)), keys outside clamped to the end cells.
+template <class K>
+__device__ __forceinline__ uint32_t bucket_less_cells(const K& k, const K* bnd, const uint16_t* flags,
+                                                      const uint16_t* cell, uint64_t kmin, uint32_t shift,
+                                                      uint32_t cbits) {
+  const uint64_t kk = (uint64_t)k;
+  uint64_t c = kk > kmin ? (kk - kmin) >> shift : 0;
+  const uint64_t last = (1u << cbits) - 1;
+  c = c < last ? c : last;
+  uint32_t lo = cell[c], hi = cell[c + 1];
+  while (lo < hi) {
+    const uint32_t mid = (lo + hi) >> 1;
+    if (KeyT<K>::lt(k, bnd[mid]))
+      hi = mid;
+    else
+      lo = mid + 1;
+  }
+  if (lo > 0 && flags[lo - 1] && KeyT<K>::eq(bnd[lo - 1], k)) return 2 * lo - 1;
+  return 2 * lo;
+}
+
 // Whether the semisort_< top level uses the wide bucket space (2^16-key
 // sample, up to 2^12 ranges, a lookup table over the key range): for
 // unsigned integer keys of up to 8 bytes, whose wide distribute buffers fit in
@@ -550,9 +572,46 @@ __global__ void __launch_bounds__(1024) k_sample(Work w, LevelBufs lb, uint32_t 
         if (reject) q = merge(false);
         if (threadIdx.x == 0 && !reject) atomicAdd((unsigned long long*)&w.ctrl->stats[12], 1ull);
       }
+      // key-cell table (integer keys): 2 n_L cells of equal key width over
+      // the range of the sample and the boundaries; cell c lists the
+      // boundaries from cell[c] (those below the cell's first key) to
+      // cell[c + 1], so a key's search covers only its own cell's boundaries
+      uint32_t cbits = 0;
+      if constexpr (KeyT<K>::kIntegral) {
+        cbits = sg.lbits + 1;
+        const uint64_t kmin = q && (uint64_t)bnd[0] < (uint64_t)S[0] ? (uint64_t)bnd[0] : (uint64_t)S[0];
+        const uint64_t kmax =
+            q && (uint64_t)bnd[q - 1] > (uint64_t)S[S_n - 1] ? (uint64_t)bnd[q - 1] : (uint64_t)S[S_n - 1];
+        const uint64_t range = kmax - kmin;
+        const uint32_t bits = range ? 64 - __clzll((long long)range) : 0;
+        const uint32_t shift = bits > cbits ? bits - cbits : 0;
+        uint16_t* cell = w.lcell[lb.level] + 2ull * sg.bbase;
+        for (uint32_t c = threadIdx.x; c <= (1u << cbits); c += blockDim.x) {
+          uint32_t v = q;
+          const uint64_t off = c < (1u << cbits) ? (uint64_t)c << shift : ~0ull;
+          if (off <= range) {
+            const K start = (K)(kmin + off);
+            uint32_t lo = 0, hi = q;  // boundaries below the cell's first key
+            while (lo < hi) {
+              const uint32_t mid = (lo + hi) >> 1;
+              if (KeyT<K>::lt(bnd[mid], start))
+                lo = mid + 1;
+              else
+                hi = mid;
+            }
+            v = lo;
+          }
+          cell[c] = (uint16_t)v;
+        }
+        if (threadIdx.x == 0) {
+          w.segs[lb.level][s].mult = kmin;
+          w.segs[lb.level][s].shift = shift;
+        }
+      }
       if (threadIdx.x == 0) {
         w.segs[lb.level][s].nh = q;
         w.segs[lb.level][s].nb = 2 * q + 1;
+        w.segs[lb.level][s].cbits = cbits;
         if (lb.level == 0) w.ctrl->stats[7] = nh;
       }
     } else {
@@ -853,6 +912,9 @@ __device__ __forceinline__ void load_heavy(const Work& w, int level, const Seg& 
 constexpr int kCountThreads = 512;
 
 // Bucket-id space of a level: the wide semisort_< top level (BIG) or the rest.
+// Cells of a narrow semisort_< level's key-cell table: 2 n_L <= 512.
+constexpr uint32_t kSegCells = 2u << (kMaxLightLog2 - 1);
+
 template <bool BIG>
 struct Space {
   static constexpr uint32_t kIds = BIG ? kBigBuckets : kMaxBuckets;   // bucket ids
@@ -869,7 +931,7 @@ struct CountSmem {
   // per key (picked by lane) so that a warp's records of one key collide at
   // most four ways in the shared-memory atomics
   unsigned long long hsum[OP == kOpReduce ? kMaxHeavy * 8 : 1];
-  uint16_t cell[BIG ? kTopCells + 1 : 1];
+  uint16_t cell[BIG ? kTopCells + 1 : OP == kOpLess ? kSegCells + 1 : 1];
 };
 
 // The wide top level's lookup table into shared memory.
@@ -880,6 +942,30 @@ __device__ __forceinline__ void load_cells(const Work& w, uint16_t* cell, uint64
     *kmin = w.toptab->kmin;
     *shift = w.toptab->shift;
   }
+}
+
+// A narrow semisort_< level's key-cell table into shared memory (integer
+// keys; sg.cbits == 0: the segment has none and the search covers all its
+// boundaries).
+template <class K, int OP, bool BIG>
+__device__ __forceinline__ void load_seg_cells(const Work& w, int level, const Seg& sg, uint16_t* cell) {
+  if constexpr (!BIG && OP == kOpLess && KeyT<K>::kIntegral) {
+    if (sg.cbits) {
+      const uint16_t* g = w.lcell[level] + 2ull * sg.bbase;
+      for (uint32_t i = threadIdx.x; i <= (1u << sg.cbits); i += blockDim.x) cell[i] = g[i];
+    }
+  }
+}
+
+// Bucket of a key at a narrow level: through the segment's key-cell table
+// when it has one.
+template <class K, int OP>
+__device__ __forceinline__ uint32_t bucket_narrow(const K& k, const Seg& sg, const K* hk, const uint16_t* ht,
+                                                  uint32_t tmask, const uint16_t* cell) {
+  if constexpr (OP == kOpLess && KeyT<K>::kIntegral) {
+    if (sg.cbits) return bucket_less_cells<K>(k, hk, ht, cell, sg.mult, sg.shift, sg.cbits);
+  }
+  return bucket_in<K, OP>(k, sg, hk, ht, tmask);
 }
 
 template <class K, class V, int OP, bool BIG>
@@ -901,6 +987,7 @@ __global__ void __launch_bounds__(kCountThreads) k_count(Work w, LevelBufs lb) {
     uint64_t tkmin = 0;
     uint32_t tshift = 0;
     load_cells<BIG && OP == kOpLess>(w, cs.cell, &tkmin, &tshift);
+    load_seg_cells<K, OP, BIG>(w, lb.level, sg, cs.cell);
     for (uint32_t b = threadIdx.x; b < nb; b += blockDim.x) hist[b] = 0;
     if (OP == kOpReduce)
       for (uint32_t b = threadIdx.x; b < sg.nh * 8; b += blockDim.x) hsum[b] = 0;
@@ -922,7 +1009,7 @@ __global__ void __launch_bounds__(kCountThreads) k_count(Work w, LevelBufs lb) {
           if constexpr (BIG && OP == kOpLess)
             b = bucket_less_tab<K>(key[u], hk, ht, cs.cell, tkmin, tshift);
           else
-            b = bucket_in<K, OP>(key[u], sg, hk, ht, tmask);
+            b = bucket_narrow<K, OP>(key[u], sg, hk, ht, tmask, cs.cell);
           atomicAdd(&hist[b], 1u);
           if constexpr (OP == kOpReduce) {
             if (b >= nl) {
@@ -1135,7 +1222,7 @@ constexpr int kDR = 16;
 constexpr int kDCH = kDT * kDR;  // 4096 records per chunk
 using DRank = BlockRank<kDT, kDR, 5>;
 
-template <class K, class V, bool BIG>
+template <class K, class V, bool BIG, int OP>
 struct DistSmem {
   RecT<K, V> S[kDCH];                // the chunk, swizzled (sw)
   typename DRank::Smem rk;
@@ -1143,7 +1230,7 @@ struct DistSmem {
   uint32_t cur[Space<BIG>::kIds];    // next write offset per bucket within the segment
   K hk[Space<BIG>::kBnd];
   uint16_t ht[Space<BIG>::kTab];
-  uint16_t cell[BIG ? kTopCells + 1 : 1];
+  uint16_t cell[BIG ? kTopCells + 1 : OP == kOpLess ? kSegCells + 1 : 1];
 };
 
 // Record i of a level's source (caller SoA at level 0, AoS records after).
@@ -1247,7 +1334,7 @@ __device__ __forceinline__ void prefetch_src(const LevelBufs& lb, uint64_t start
 template <class K, class V, int OP, bool BIG>
 __global__ void __launch_bounds__(kDT, 2) k_distribute(Work w, LevelBufs lb) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
-  DistSmem<K, V, BIG>& sm = *reinterpret_cast<DistSmem<K, V, BIG>*>(smem_raw);
+  DistSmem<K, V, BIG, OP>& sm = *reinterpret_cast<DistSmem<K, V, BIG, OP>*>(smem_raw);
   using Rec = RecT<K, V>;
   constexpr int RB = sizeof(Rec);
   constexpr bool kVals = !std::is_same<V, void>::value;
@@ -1313,6 +1400,7 @@ __global__ void __launch_bounds__(kDT, 2) k_distribute(Work w, LevelBufs lb) {
     uint64_t tkmin = 0;
     uint32_t tshift = 0;
     load_cells<BIG && OP == kOpLess>(w, sm.cell, &tkmin, &tshift);
+    load_seg_cells<K, OP, BIG>(w, lb.level, sg, sm.cell);
     {
       const uint32_t* X = w.C[lb.level] + sg.cbase;
       const uint32_t* boff = w.boff[lb.level] + sg.bbase;
@@ -1346,7 +1434,7 @@ __global__ void __launch_bounds__(kDT, 2) k_distribute(Work w, LevelBufs lb) {
           } else if constexpr (BIG) {
             bid[r] = bucket_less_tab<K>(sm.S[sw<RB>(c0t + r)].k, sm.hk, sm.ht, sm.cell, tkmin, tshift);
           } else {
-            bid[r] = bucket_in<K, OP>(sm.S[sw<RB>(c0t + r)].k, sg, sm.hk, sm.ht, tmask);
+            bid[r] = bucket_narrow<K, OP>(sm.S[sw<RB>(c0t + r)].k, sg, sm.hk, sm.ht, tmask, sm.cell);
           }
         }
       }

@@ -89,11 +89,11 @@ cudaError_t launch_pipeline(const Plan& P, const Work& w, cudaStream_t st, const
   const int nsm = cfg.num_sms;
   constexpr bool kWide = TopWide<K, OP>::value;  // semisort_< top level in the wide bucket space
   constexpr size_t kSmemMax = 232448;              // opt-in shared memory per block (sm_103a)
-  static_assert(sizeof(DistSmem<K, V, false>) <= kSmemMax && sizeof(DistSmem<K, V, kWide>) <= kSmemMax, "smem");
+  static_assert(sizeof(DistSmem<K, V, false, OP>) <= kSmemMax && sizeof(DistSmem<K, V, kWide, OP>) <= kSmemMax, "smem");
   static_assert(sizeof(CountSmem<K, OP, kWide>) <= kSmemMax && sizeof(RefSmem<K, V>) <= kSmemMax, "smem");
   static_assert(sizeof(LessSmem<K, V>) <= kSmemMax && sizeof(RedSmem<K>) <= kSmemMax, "smem");
-  const size_t dist_smem = sizeof(DistSmem<K, V, false>);
-  const size_t dist_smem_top = sizeof(DistSmem<K, V, kWide>);
+  const size_t dist_smem = sizeof(DistSmem<K, V, false, OP>);
+  const size_t dist_smem_top = sizeof(DistSmem<K, V, kWide, OP>);
   const size_t count_smem = sizeof(CountSmem<K, OP, false>);
   const size_t count_smem_top = sizeof(CountSmem<K, OP, kWide>);
   size_t ref_smem = 0;

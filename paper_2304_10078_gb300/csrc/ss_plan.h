@@ -76,7 +76,7 @@ struct Seg {
   uint32_t shift;      // identity hashing: first key bit of this segment's light-bucket id
   uint32_t ident;      // bucket ids from the key's own bits (identity hash)
   uint32_t nl;         // light buckets n_L (a power of two, or 768)
-  uint32_t pad;
+  uint32_t cbits;      // semisort_<, integer keys: log2 of the key-cell table's cells (0: no table)
 };
 
 struct Tile {
@@ -152,6 +152,7 @@ struct Work {
   uint64_t* num_unique; // user pointer (collect-reduce / histogram)
   void* sums_out;       // user pointer: u64 sums or u32 counts
   void* splitters[kMaxLevels];  // semisort_<: per-segment sorted boundaries at bbase
+  uint16_t* lcell[kMaxLevels];  // semisort_<, integer keys: per-segment key-cell tables at 2*bbase
   void* bigs;           // semisort_<: the sorted top-level sample (kBigSample keys)
   void* bigs_tmp;       // its sorted runs before the merge
   void* learn;          // semisort_<: learned-splitter state (LearnState)
@@ -180,7 +181,7 @@ struct Plan {
   size_t off_tk, off_tv, off_t2k, off_t2v;
   size_t off_segs[kMaxLevels], off_tiles[kMaxLevels], off_C[kMaxLevels], off_hkeys[kMaxLevels],
       off_htab[kMaxLevels], off_bsize[kMaxLevels], off_boff[kMaxLevels], off_hpart[kMaxLevels],
-      off_split[kMaxLevels];
+      off_split[kMaxLevels], off_lcell[kMaxLevels];
   size_t off_items, off_item_out, off_item_pos, off_block_sums, off_ctrl, off_scratch32, off_item_aux;
   size_t off_bigs, off_bigs_tmp, off_learn, off_inst_base, off_inst_first, off_toptab;
   uint32_t num_inst;

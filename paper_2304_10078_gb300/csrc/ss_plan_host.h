@@ -144,6 +144,10 @@ inline ss_status plan_workspace(int op, int kbytes, int vbytes, size_t recbytes,
     o = al(o + (op == SS_OP_COLLECT_REDUCE ? (size_t)P->c_cap[l] * 8 : 0));
     P->off_split[l] = o;
     o = al(o + (less ? (size_t)P->bucket_cap[l] * P->kbytes : 0));
+    // key-cell tables of the narrow semisort_< levels: 2 n_L + 1 cells per
+    // segment within its 4 n_L bucket rows (two u16 per row)
+    P->off_lcell[l] = o;
+    o = al(o + (less && integral ? (size_t)P->bucket_cap[l] * 4 : 0));
   }
   if (!multi) P->item_cap = std::max<uint32_t>(1, num_inst);
   P->off_items = o;
@@ -202,6 +206,7 @@ inline void fill_work(const Plan& P, void* ws, Work* w) {
     w->boff[l] = reinterpret_cast<uint32_t*>(b + P.off_boff[l]);
     w->hpart[l] = reinterpret_cast<uint64_t*>(b + P.off_hpart[l]);
     w->splitters[l] = b + P.off_split[l];
+    w->lcell[l] = reinterpret_cast<uint16_t*>(b + P.off_lcell[l]);
     w->seg_cap[l] = P.seg_cap[l];
     w->tile_cap[l] = P.tile_cap[l];
     w->c_cap[l] = P.c_cap[l];
