@@ -168,6 +168,42 @@ __device__ __forceinline__ uint64_t block_exclusive_scan64(uint64_t v, uint64_t*
   return r;
 }
 
+// Maximum of v over the threads before this one (0 for thread 0), and
+// minimum over the threads after it (0xFFFFFFFF for the last); `tmp` holds
+// at least 32 words.  Both contain __syncthreads.
+__device__ __forceinline__ uint32_t block_exclusive_max(uint32_t v, uint32_t* tmp) {
+  const int lane = threadIdx.x & 31, w = threadIdx.x >> 5, nw = (blockDim.x + 31) >> 5;
+  uint32_t inc = v;
+#pragma unroll
+  for (int o = 1; o < 32; o <<= 1) {
+    const uint32_t t = __shfl_up_sync(kFull, inc, o);
+    if (lane >= o) inc = t > inc ? t : inc;
+  }
+  uint32_t ex = __shfl_up_sync(kFull, inc, 1);
+  if (lane == 0) ex = 0;
+  if (lane == 31) tmp[w] = inc;
+  __syncthreads();
+  for (int j = 0; j < w && j < nw; ++j) ex = tmp[j] > ex ? tmp[j] : ex;
+  __syncthreads();
+  return ex;
+}
+__device__ __forceinline__ uint32_t block_suffix_min(uint32_t v, uint32_t* tmp) {
+  const int lane = threadIdx.x & 31, w = threadIdx.x >> 5, nw = (blockDim.x + 31) >> 5;
+  uint32_t inc = v;
+#pragma unroll
+  for (int o = 1; o < 32; o <<= 1) {
+    const uint32_t t = __shfl_down_sync(kFull, inc, o);
+    if (lane + o < 32) inc = t < inc ? t : inc;
+  }
+  uint32_t ex = __shfl_down_sync(kFull, inc, 1);
+  if (lane == 31) ex = 0xFFFFFFFFu;
+  if (lane == 0) tmp[w] = inc;
+  __syncthreads();
+  for (int j = w + 1; j < nw; ++j) ex = tmp[j] < ex ? tmp[j] : ex;
+  __syncthreads();
+  return ex;
+}
+
 __device__ __forceinline__ uint32_t block_reduce_sum(uint32_t v, uint32_t* tmp) {
   uint32_t t;
   block_exclusive_scan(v, tmp, &t);

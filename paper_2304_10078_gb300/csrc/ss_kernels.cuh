@@ -1937,23 +1937,27 @@ __global__ void __launch_bounds__(kRT, 2) k_finish_equal(Work w) {
 // finish (semisort_<): the base case of Sec. 3.3 with a sort by key, and the
 // copy-backs of Sec. 3.4.  A window's records are staged once in shared
 // memory.  For keys up to 8 bytes every record gets an interpolation bucket,
-// the top 12 bits of (key - window minimum), a non-decreasing function of the
+// the top 15 bits of (key - window minimum), a non-decreasing function of the
 // key; a stable rank by it (at most three 5-bit passes) leaves the window
-// ordered by bucket with input order inside each bucket, and an insertion sort
-// (stable) finishes every run of equal buckets.  Runs are short unless keys
-// repeat (then they are already in order) or cluster; a window with a long
-// unordered run -- and every window of 128-bit or user-defined keys -- is sorted instead by
-// Batcher's bitonic network on (key, position in the window).  Either way the
-// output is the stable sort of the window.
+// ordered by bucket with input order inside each bucket.  Runs of equal
+// buckets that hold an inversion are then ordered in parallel: every record
+// counts the records of its run that precede it by (key, window index).
+// Runs are short unless keys repeat (then they are already in order) or
+// cluster; a window with an unordered run longer than 64 records -- and every
+// window of 128-bit or user-defined keys -- is sorted instead by Batcher's
+// bitonic network on (key, position in the window).  Either way the output
+// is the stable sort of the window.
 // ----------------------------------------------------------------------------
 template <class K, class V>
 struct LessSmem {
   RecT<K, V> S[kRefMax];  // the window, swizzled (sw)
   union {
     typename RRank::Smem rk;
-    uint16_t idx[kRefMax];  // bitonic: positions in the window
+    uint16_t idx[kRefMax];                 // bitonic: positions in the window
+    uint32_t px2[kRefMax + kRefMax / 32];  // the final order, padded (bpad)
   } u;
   uint32_t px[kRefMax + kRefMax / 32];  // (bucket << 16 | index) at rank, padded (bpad)
+  uint8_t runinv[kRefMax];              // per run start: the run holds an inversion
   uint32_t scan_tmp[33];
   unsigned long long mn[32], mx[32];
   uint32_t fallback;
@@ -2023,8 +2027,8 @@ __global__ void __launch_bounds__(kRT, 2) k_finish_less(Work w) {
       }
       const uint64_t range = hi - lo;
       const uint32_t bits = range ? 64 - __clzll((long long)range) : 0;
-      const uint32_t shift = bits > 12 ? bits - 12 : 0;
-      const uint32_t nbits = bits - shift;  // bucket ids < 2^nbits <= 4096
+      const uint32_t shift = bits > 15 ? bits - 15 : 0;
+      const uint32_t nbits = bits - shift;  // bucket ids < 2^nbits <= 2^15
       if (nbits == 0) {
         // all keys equal: the window is already sorted
         for (uint32_t p = tid; p < m; p += kRT) store_out<K, V>(w, it.start + p, sm.S[sw<RB>(p)]);
@@ -2039,51 +2043,92 @@ __global__ void __launch_bounds__(kRT, 2) k_finish_less(Work w) {
         g[r] = (ib << 16) | c;
       }
       rank_window(sm.u.rk, sm.px, g, (nbits + 4) / 5, c0t);
-      // finish every run of equal buckets by a stable insertion sort on the key.
-      // With shift 0 a bucket holds one key value: the rank is already the sort.
-      // Otherwise look for an out-of-order neighbour first (in parallel).
+      // Runs of equal buckets are in window order.  With shift 0 a bucket
+      // holds one key value and the rank is already the sort; otherwise find
+      // the inversions (a key below its predecessor's in the same run), in
+      // blocked order.
       auto key_at = [&](uint32_t x) { return sm.S[sw<RB>(x & 0xFFFFu)].k; };
-      bool any = false;
+      uint32_t headm = 0, invm = 0;
       if (shift > 0) {
-        for (uint32_t p = 1 + tid; p < m; p += kRT) {
-          const uint32_t x = sm.px[bpad(p)], y = sm.px[bpad(p - 1)];
-          if ((x >> 16) == (y >> 16) && KeyT<K>::lt(key_at(x), key_at(y))) any = true;
+        uint32_t pb = 0xFFFFFFFFu;
+        K pk{};
+        if (c0t > 0 && c0t - 1 < m) {
+          const uint32_t x = sm.px[bpad(c0t - 1)];
+          pb = x >> 16;
+          pk = key_at(x);
+        }
+#pragma unroll
+        for (int r = 0; r < kRR; ++r) {
+          const uint32_t p = c0t + r;
+          if (p < m) {
+            const uint32_t x = sm.px[bpad(p)];
+            const K k = key_at(x);
+            const bool head = (x >> 16) != pb;
+            headm |= head ? 1u << r : 0u;
+            invm |= (!head && KeyT<K>::lt(k, pk)) ? 1u << r : 0u;
+            pb = x >> 16;
+            pk = k;
+          }
         }
       }
-      if (!__syncthreads_or(any)) {
+      if (!__syncthreads_or(invm != 0)) {
         for (uint32_t p = tid; p < m; p += kRT)
           store_out<K, V>(w, it.start + p, sm.S[sw<RB>(sm.px[bpad(p)] & 0xFFFFu)]);
         __syncthreads();
         continue;
       }
-      for (uint32_t p = tid; p < m; p += kRT) {
-        const uint32_t b = sm.px[bpad(p)] >> 16;
-        if (p > 0 && (sm.px[bpad(p - 1)] >> 16) == b) continue;  // not a run start
-        uint32_t e = p + 1;
-        while (e < m && (sm.px[bpad(e)] >> 16) == b) ++e;
-        if (e - p < 2) continue;
-        if (e - p > 64) {
-          bool sorted = true;
-          for (uint32_t i = p + 1; i < e && sorted; ++i)
-            sorted = !KeyT<K>::lt(key_at(sm.px[bpad(i)]), key_at(sm.px[bpad(i - 1)]));
-          if (!sorted) sm.fallback = 1;
-          continue;
-        }
-        for (uint32_t i = p + 1; i < e; ++i) {
-          const uint32_t x = sm.px[bpad(i)];
-          const K kx = key_at(x);
-          uint32_t j = i;
-          while (j > p && KeyT<K>::lt(kx, key_at(sm.px[bpad(j - 1)]))) {
-            sm.px[bpad(j)] = sm.px[bpad(j - 1)];
-            --j;
-          }
-          sm.px[bpad(j)] = x;
-        }
+      // Run bounds: the run of position p starts at the last head at or
+      // before p and ends before the first head after p (block-wide max and
+      // suffix-min scans over the threads' head positions).
+      const uint32_t hfirst = headm ? c0t + __ffs(headm) - 1 : 0xFFFFFFFFu;
+      const uint32_t hlast = headm ? c0t + 31 - __clz(headm) : 0u;
+      uint32_t rs = block_exclusive_max(hlast, sm.scan_tmp);
+      uint32_t nh = block_suffix_min(hfirst, sm.scan_tmp);
+      nh = nh < m ? nh : m;
+#pragma unroll
+      for (int r = 0; r < kRR; ++r)
+        if (headm >> r & 1u) sm.runinv[c0t + r] = 0;
+      __syncthreads();
+      uint32_t rsr[kRR];
+#pragma unroll
+      for (int r = 0; r < kRR; ++r) {
+        if (headm >> r & 1u) rs = c0t + r;
+        rsr[r] = rs;
+        if (invm >> r & 1u) sm.runinv[rs] = 1;
       }
       __syncthreads();
-      if (!sm.fallback) {
+      // Every record of a run with an inversion takes its place in the run
+      // by (key, window index): the records of the run before it with a key
+      // not above its own, and those after it with a smaller key, precede
+      // it.  Runs longer than kRunMax go to the bitonic network instead.
+      constexpr uint32_t kRunMax = 64;
+      uint32_t longrun = 0;
+      uint32_t re = nh;
+#pragma unroll
+      for (int r = kRR - 1; r >= 0; --r) {
+        const uint32_t p = c0t + r;
+        if (p >= m) continue;
+        const uint32_t x = sm.px[bpad(p)];
+        uint32_t pos = p;
+        if (sm.runinv[rsr[r]]) {
+          if (re - rsr[r] > kRunMax) {
+            longrun = 1;
+          } else {
+            const K kp = key_at(x);
+            pos = rsr[r];
+            for (uint32_t q = rsr[r]; q < re; ++q) {
+              if (q == p) continue;
+              const K kq = key_at(sm.px[bpad(q)]);
+              pos += q < p ? (KeyT<K>::lt(kp, kq) ? 0u : 1u) : (KeyT<K>::lt(kq, kp) ? 1u : 0u);
+            }
+          }
+        }
+        sm.u.px2[bpad(pos)] = x;
+        if (headm >> r & 1u) re = p;
+      }
+      if (!__syncthreads_or(longrun)) {
         for (uint32_t p = tid; p < m; p += kRT)
-          store_out<K, V>(w, it.start + p, sm.S[sw<RB>(sm.px[bpad(p)] & 0xFFFFu)]);
+          store_out<K, V>(w, it.start + p, sm.S[sw<RB>(sm.u.px2[bpad(p)] & 0xFFFFu)]);
         __syncthreads();
         continue;
       }
