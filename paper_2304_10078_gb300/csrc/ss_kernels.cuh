@@ -1267,6 +1267,23 @@ __device__ __forceinline__ void load_chunk(RecT<K, V>* S, uint32_t len, Src src)
 }
 
 
+// Asynchronous global -> shared copy of `bytes` (4, 8 or 16, both addresses
+// aligned to it) that bypasses registers; async_wait() waits for all of the
+// thread's copies (a barrier must follow before other threads read them).
+template <int bytes>
+__device__ __forceinline__ void async_copy(void* smem_dst, const void* gmem_src) {
+  static_assert(bytes == 4 || bytes == 8 || bytes == 16, "cp.async size");
+  const uint32_t sa = (uint32_t)__cvta_generic_to_shared(smem_dst);
+  if constexpr (bytes == 16)
+    asm volatile("cp.async.cg.shared.global [%0], [%1], 16;" ::"r"(sa), "l"(gmem_src) : "memory");
+  else
+    asm volatile("cp.async.ca.shared.global [%0], [%1], %2;" ::"r"(sa), "l"(gmem_src), "n"(bytes) : "memory");
+}
+__device__ __forceinline__ void async_wait() {
+  asm volatile("cp.async.commit_group;" ::: "memory");
+  asm volatile("cp.async.wait_group 0;" ::: "memory");
+}
+
 // Hash-bucket ids of a thread's kDR records in one pass: every light bucket
 // first (no branches), then the first heavy-table probe of every record as
 // independent loads, then the rare longer probe chains.
@@ -1821,6 +1838,23 @@ __device__ __forceinline__ void rank_window(typename RRank::Smem& rs, uint32_t* 
   __syncthreads();
 }
 
+// A base-case window into the swizzled shared buffer: records of a
+// temporary array (16-byte records) by asynchronous copies, all of a thread's
+// copies in flight at once; other windows through registers.
+template <class K, class V>
+__device__ __forceinline__ void load_window(RecT<K, V>* S, const Work& w, const Item& it) {
+  using Rec = RecT<K, V>;
+  constexpr int RB = sizeof(Rec);
+  if (RB == 16 && it.buf != kBufIn && it.buf != kBufOut) {
+    const Rec* src = reinterpret_cast<const Rec*>(buf_ptr(w, it.buf)) + it.start;
+    for (uint32_t i = threadIdx.x; i < it.len; i += blockDim.x) async_copy<16>(&S[sw<RB>(i)], src + i);
+    async_wait();
+  } else {
+    auto ld = [&](uint32_t i) { return load_rec<K, V>(w, it.buf, it.start + i); };
+    load_chunk<kRT, K, V, decltype(ld), 16, 4>(S, it.len, ld);
+  }
+}
+
 // L2 prefetch of a refine window's records.
 template <class K, class V>
 __device__ __forceinline__ void prefetch_item(const Work& w, const Item& it) {
@@ -1879,10 +1913,7 @@ __global__ void __launch_bounds__(kRT, 2) k_finish_equal(Work w) {
     if (next_window(w, itx + gridDim.x, nfin, &nx)) prefetch_item<K, V>(w, nx);
     uint32_t ts = 64;
     while (ts < 2 * m) ts <<= 1;
-    {
-      auto ld = [&](uint32_t i) { return load_rec<K, V>(w, it.buf, it.start + i); };
-      load_chunk<kRT, K, V, decltype(ld), 16, 4>(sm.S, m, ld);
-    }
+    load_window<K, V>(sm.S, w, it);
     for (uint32_t i = tid; i < ts; i += kRT) sm.u.table[i] = kEmpty;
     __syncthreads();
     first_occurrences<K>(sm.u.table, 31 - __clz(ts), m, c0t, salt,
@@ -1988,8 +2019,7 @@ __global__ void __launch_bounds__(kRT, 2) k_finish_less(Work w) {
       Item nx;  // the next window streams into L2 while this one is sorted
       if (next_window(w, itx + gridDim.x, nfin, &nx)) prefetch_item<K, V>(w, nx);
     }
-    auto ld = [&](uint32_t i) { return load_rec<K, V>(w, it.buf, it.start + i); };
-    load_chunk<kRT, K, V, decltype(ld), 16, 4>(sm.S, m, ld);
+    load_window<K, V>(sm.S, w, it);
     if (tid == 0) {
       sm.fallback = KeyT<K>::kIntegral ? 0u : 1u;
       atomicAdd((unsigned long long*)&w.ctrl->stats[5], (unsigned long long)m);
@@ -2237,9 +2267,16 @@ __global__ void __launch_bounds__(kRT, 2) k_finish_reduce(Work w) {
     }
     uint32_t ts = 64;
     while (ts < 2 * m) ts <<= 1;
-    for (uint32_t c = tid; c < m; c += kRT)
-      sm.keys[c] = it.buf == kBufIn ? reinterpret_cast<const K*>(w.in_k)[it.start + c]
-                                    : reinterpret_cast<const Rec*>(buf_ptr(w, it.buf))[it.start + c].k;
+    if (sizeof(K) == 8 && it.buf != kBufIn) {
+      // keys of a temporary array's records: asynchronous 8-byte copies
+      const Rec* src = reinterpret_cast<const Rec*>(buf_ptr(w, it.buf)) + it.start;
+      for (uint32_t c = tid; c < m; c += kRT) async_copy<8>(&sm.keys[c], &src[c].k);
+      async_wait();
+    } else {
+      for (uint32_t c = tid; c < m; c += kRT)
+        sm.keys[c] = it.buf == kBufIn ? reinterpret_cast<const K*>(w.in_k)[it.start + c]
+                                      : reinterpret_cast<const Rec*>(buf_ptr(w, it.buf))[it.start + c].k;
+    }
     for (uint32_t i = tid; i < ts; i += kRT) sm.table[i] = kEmpty;
     __syncthreads();
     uint32_t lab[kRR];
