@@ -2292,6 +2292,31 @@ __global__ void __launch_bounds__(kRT, 2) k_finish_reduce(Work w) {
     }
     uint32_t G;
     uint32_t g0 = block_exclusive_scan(nfirst, sm.scan_tmp, &G);
+    if (G == m) {
+      // every key distinct: each record is its own group, and the compacted
+      // window is the window itself -- already in place in a temporary
+      // array; a window of the caller's input is copied to T
+      if (it.buf == kBufIn) {
+        Rec* cb = reinterpret_cast<Rec*>(buf_ptr(w, compact_buf(it.buf)));
+        for (uint32_t c = tid; c < m; c += kRT) {
+          Rec o;
+          o.k = sm.keys[c];
+          if constexpr (OP == kOpReduce) o.v = reinterpret_cast<const uint64_t*>(w.in_v)[it.start + c];
+          cb[it.start + c] = o;
+        }
+      }
+      if constexpr (OP == kOpHist)
+        for (uint32_t c = tid; c < m; c += kRT) w.scratch32[it.start + c] = 1u;
+      if (tid == 0) {
+        w.item_out[itx] = G;
+        atomicAdd((unsigned long long*)&w.ctrl->stats[5], (unsigned long long)m);
+        atomicAdd((unsigned long long*)&w.ctrl->stats[9], 1ull);
+        atomicMax((unsigned long long*)&w.ctrl->stats[8], (unsigned long long)m);
+        atomicAdd((unsigned long long*)&w.ctrl->stats[10], (unsigned long long)m);
+      }
+      __syncthreads();
+      continue;
+    }
 #pragma unroll
     for (int r = 0; r < kRR; ++r) {
       const uint32_t c = c0t + r;
