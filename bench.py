@@ -584,20 +584,26 @@ def bench_sweeps(ss, sg, torch, stream, reps=3):
     return out
 
 
-def e2e_pipelined(ss, torch, hk, hv, n, steps, ws, opt):
+def e2e_pipelined(ss, torch, hk, hv, n, steps, ws, opt, hko=None, hvo=None):
     """End to end through the public API with host buffers: every step copies
     its input (keys, values) from pinned host memory to the device, runs
     semisort_=, and copies the output back to pinned host memory.  Steps are
     pipelined on three streams with two device buffer sets, so step i+1's
     upload and step i-1's download overlap step i's call; all copies are
-    inside the timed region."""
+    inside the timed region.  One untimed step first warms the copy path."""
     u64 = torch.uint64
     s_cmp = torch.cuda.current_stream()
     s_in, s_out = torch.cuda.Stream(), torch.cuda.Stream()
     din = [(torch.empty(n, dtype=u64, device="cuda"), torch.empty(n, dtype=u64, device="cuda")) for _ in range(2)]
     dout = [(torch.empty(n, dtype=u64, device="cuda"), torch.empty(n, dtype=u64, device="cuda")) for _ in range(2)]
-    hko = torch.empty(n, dtype=u64, pin_memory=True)
-    hvo = torch.empty(n, dtype=u64, pin_memory=True)
+    if hko is None:
+        hko = torch.empty(n, dtype=u64, pin_memory=True)
+        hvo = torch.empty(n, dtype=u64, pin_memory=True)
+    din[0][0].copy_(hk, non_blocking=True)
+    din[0][1].copy_(hv, non_blocking=True)
+    ss.semisort_equal(din[0][0], din[0][1], keys_out=dout[0][0], vals_out=dout[0][1], workspace=ws, options=opt)
+    hko.copy_(dout[0][0], non_blocking=True)
+    hvo.copy_(dout[0][1], non_blocking=True)
     ev = lambda: torch.cuda.Event()
     ev_in, ev_cmp, ev_out = [ev(), ev()], [ev(), ev()], [ev(), ev()]
     torch.cuda.synchronize()
@@ -647,7 +653,7 @@ def main():
                     help="records per distribution for the all-core oracle leg (0: skip both CPU legs)")
     ap.add_argument("--cpu-scale-sample", type=int, default=1 << 24,
                     help="records per distribution for the single-thread scale point (0: skip)")
-    ap.add_argument("--e2e-steps", type=int, default=4)
+    ap.add_argument("--e2e-steps", type=int, default=8)
     ap.add_argument("--dists", default="", help="comma-separated indices into the distribution list")
     ap.add_argument("--ops", default="collect_reduce,histogram,semisort_equal_identity,semisort_equal_swap,"
                                       "semisort_less,"
@@ -674,6 +680,11 @@ def main():
     ss.lib()
     n = args.n
     dists = [DISTS[int(i)] for i in args.dists.split(",")] if args.dists else DISTS
+    # pinned host buffers of the end-to-end leg, allocated before the large
+    # device allocations (their placement then matches a standalone run)
+    e2e_host = None
+    if rank == 0 and args.e2e_steps > 0:
+        e2e_host = [torch.empty(n, dtype=torch.uint64, pin_memory=True) for _ in range(4)]
     # device-resident inputs: one key array per distribution, one value array
     keys = []
     vals = sg.iota(n)
@@ -767,18 +778,17 @@ def main():
     cpu = None
     if rank == 0 and args.e2e_steps > 0:
         d_i = next((i for i, d in enumerate(dists) if d == ("zipf", 1.2)), len(dists) - 1)
-        hk = torch.empty(n, dtype=torch.uint64, pin_memory=True)
-        hv = torch.empty(n, dtype=torch.uint64, pin_memory=True)
+        hk, hv, hko, hvo = e2e_host
         hk.copy_(keys[d_i])
         hv.copy_(vals)
         del kout, vout
         torch.cuda.empty_cache()
-        v_e2e, t_e2e, ok = e2e_pipelined(ss, torch, hk, hv, n, args.e2e_steps, ws, opt)
+        v_e2e, t_e2e, ok = e2e_pipelined(ss, torch, hk, hv, n, args.e2e_steps, ws, opt, hko, hvo)
         e2e = {"value": v_e2e, "unit": UNIT, "h2d_bytes_per_step": 16 * n, "d2h_bytes_per_step": 16 * n,
                "workload": f"semisort_equal n={n} {dist_name(dists[d_i])}, {args.e2e_steps} steps pipelined "
                            "(upload, call, download on three streams, two device buffer sets)",
                "seconds": t_e2e, "download_check": ok}
-        del hk, hv
+        del hk, hv, hko, hvo, e2e_host
     if rank == 0 and args.cpu_sample:
         cpu = cpu_oracle_all_cores(torch, keys, vals, dists, args.cpu_sample)
     if "batched" in ops or "rmat_csr" in ops or "sweeps" in ops:

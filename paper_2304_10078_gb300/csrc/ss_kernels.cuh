@@ -968,7 +968,10 @@ __device__ __forceinline__ uint32_t bucket_narrow(const K& k, const Seg& sg, con
   return bucket_in<K, OP>(k, sg, hk, ht, tmask);
 }
 
-template <class K, class V, int OP, bool BIG>
+// U: keys in flight per thread -- 16 from the caller's key array (level 0),
+// 4 from the temporaries' 16-byte records (deeper levels, where the smaller
+// register footprint keeps four CTAs per SM), as measured.
+template <class K, class V, int OP, bool BIG, int U>
 __global__ void __launch_bounds__(kCountThreads) k_count(Work w, LevelBufs lb) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
   CountSmem<K, OP, BIG>& cs = *reinterpret_cast<CountSmem<K, OP, BIG>*>(smem_raw);
@@ -992,7 +995,6 @@ __global__ void __launch_bounds__(kCountThreads) k_count(Work w, LevelBufs lb) {
     if (OP == kOpReduce)
       for (uint32_t b = threadIdx.x; b < sg.nh * 8; b += blockDim.x) hsum[b] = 0;
     __syncthreads();
-    constexpr int U = 4;
     const uint32_t per = blockDim.x * U;
     for (uint32_t i0 = 0; i0 < tl.len; i0 += per) {
       K key[U];

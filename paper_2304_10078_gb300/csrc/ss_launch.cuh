@@ -100,8 +100,9 @@ cudaError_t launch_pipeline(const Plan& P, const Work& w, cudaStream_t st, const
   cudaError_t e;
   if ((e = set_smem(k_distribute<K, V, OP, false>, dist_smem)) != cudaSuccess) return e;
   if ((e = set_smem(k_distribute<K, V, OP, kWide>, dist_smem_top)) != cudaSuccess) return e;
-  if ((e = set_smem(k_count<K, V, OP, false>, count_smem)) != cudaSuccess) return e;
-  if ((e = set_smem(k_count<K, V, OP, kWide>, count_smem_top)) != cudaSuccess) return e;
+  if ((e = set_smem(k_count<K, V, OP, false, 4>, count_smem)) != cudaSuccess) return e;
+  if ((e = set_smem(k_count<K, V, OP, false, 16>, count_smem)) != cudaSuccess) return e;
+  if ((e = set_smem(k_count<K, V, OP, kWide, 16>, count_smem_top)) != cudaSuccess) return e;
   const size_t bigs_smem = (size_t)BigRun<K>::len * sizeof(K);
   const size_t split_smem = less_split_smem<K>();
   if constexpr (kWide) {
@@ -178,9 +179,11 @@ cudaError_t launch_pipeline(const Plan& P, const Work& w, cudaStream_t st, const
       }
       if (tm) tm->mark(level == 0 ? "sample.L0" : "sample.L1+");
       if (top_wide)
-        k_count<K, V, OP, kWide><<<cap(tiles, nsm * 4), kCountThreads, count_smem_top, st>>>(w, lb);
+        k_count<K, V, OP, kWide, 16><<<cap(tiles, nsm * 4), kCountThreads, count_smem_top, st>>>(w, lb);
+      else if (lb.src_aos)
+        k_count<K, V, OP, false, 4><<<cap(tiles, nsm * 4), kCountThreads, count_smem, st>>>(w, lb);
       else
-        k_count<K, V, OP, false><<<cap(tiles, nsm * 4), kCountThreads, count_smem, st>>>(w, lb);
+        k_count<K, V, OP, false, 16><<<cap(tiles, nsm * 4), kCountThreads, count_smem, st>>>(w, lb);
       if (tm) tm->mark(level == 0 ? "count.L0" : "count.L1+");
       k_scan<OP><<<cap(segs, nsm * 2), 1024, 0, st>>>(w, lb);
       if (tm) tm->mark(level == 0 ? "scan.L0" : "scan.L1+");
