@@ -148,3 +148,39 @@ def test_clustered_keys(ss, n):
     vals = np.arange(n, dtype=np.uint64)
     ko, vo, _ = run_less(ss, keys, vals)
     check(keys, vals, ko, vo)
+
+
+def _window_with_runs(seed, n, runs, dup):
+    """One base-case window (n <= alpha) whose keys span [0, 2^40): the
+    interpolation bucket of the base case is then 2^25 keys wide, and each
+    entry L of `runs` puts L keys into one bucket (its own) in an order with
+    inversions -- descending distinct keys, or (dup) three key values
+    interleaved, so equal keys also test stability.  The other keys are
+    spread over the range."""
+    rng = np.random.default_rng(seed)
+    parts = [np.array([0, (1 << 40) - 1], dtype=np.uint64)]
+    for j, L in enumerate(runs):
+        base = np.uint64((8 + 64 * j) << 25)
+        if dup:
+            k = base + rng.integers(0, 3, size=L, dtype=np.uint64) * np.uint64(1 << 20)
+        else:
+            k = base + (np.arange(L, 0, -1, dtype=np.uint64) * np.uint64(7))
+        parts.append(k)
+    rest = n - sum(len(p) for p in parts)
+    parts.append(rng.integers(0, 1 << 40, size=rest, dtype=np.uint64))
+    # a random order of all keys keeps inversions inside every run
+    return np.concatenate(parts)[rng.permutation(n)]
+
+
+@pytest.mark.parametrize("runs", [[2], [63, 64], [65], [64, 65, 64], [200], [1000, 3]])
+@pytest.mark.parametrize("dup", [False, True])
+def test_base_case_unordered_runs(ss, runs, dup):
+    """Runs of equal interpolation buckets that hold inversions: up to 64
+    records they are ordered in parallel, longer ones send the window to the
+    bitonic network; either way the output is the stable sort."""
+    n = 4096
+    keys = _window_with_runs(7 + len(runs) + (100 if dup else 0), n, runs, dup)
+    vals = np.arange(n, dtype=np.uint64)
+    ko, vo, st = run_less(ss, keys, vals)
+    check(keys, vals, ko, vo)
+    assert st["refined"] == n
