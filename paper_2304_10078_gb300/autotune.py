@@ -6,6 +6,12 @@ launching stream, one warm-up call per candidate).  Choices are cached per
 
 Only the speed depends on these settings; every candidate gives the same
 result class (exact semisort / reduce), so tuning never changes correctness.
+
+The choice applies to the whole batch (one options struct per call): l and
+alpha are batch-wide, while every instance's n_L follows its own size (the
+planning kernel sets n_L from 2 m / alpha per segment; n_light_log2 steers
+only a single instance's top level), so a 2^8-record and a 2^22-record
+instance of one batch do not share a bucket count.
 """
 from __future__ import annotations
 
