@@ -1993,7 +1993,6 @@ struct LessSmem {
   uint8_t runinv[kRefMax];              // per run start: the run holds an inversion
   uint32_t scan_tmp[33];
   unsigned long long mn[32], mx[32];
-  uint32_t fallback;
 };
 
 template <class K, class V>
@@ -2023,7 +2022,6 @@ __global__ void __launch_bounds__(kRT, 2) k_finish_less(Work w) {
     }
     load_window<K, V>(sm.S, w, it);
     if (tid == 0) {
-      sm.fallback = KeyT<K>::kIntegral ? 0u : 1u;
       atomicAdd((unsigned long long*)&w.ctrl->stats[5], (unsigned long long)m);
       atomicAdd((unsigned long long*)&w.ctrl->stats[9], 1ull);
       atomicMax((unsigned long long*)&w.ctrl->stats[8], (unsigned long long)m);
