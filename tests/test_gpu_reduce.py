@@ -162,3 +162,19 @@ def test_parameters(ss, alpha, subarray, lbits):
     uk, out, u, err, _ = run_reduce(ss, keys, vals, alpha=alpha, subarray=subarray, n_light_log2=lbits)
     assert err == 0
     check(keys, vals, uk, out, u)
+
+
+@pytest.mark.parametrize("n", [2, 100, 4096])
+@pytest.mark.parametrize("op", ["reduce", "hist"])
+def test_single_window_all_distinct(ss, n, op):
+    """n <= alpha: the whole input is one base case read from the caller's
+    arrays; with all keys distinct the window is its own output and is copied
+    to the temporary before the pack (the in-place shortcut applies only to
+    windows already in a temporary)."""
+    keys = synth.splitmix64_outputs(60 + n, n)
+    vals = None if op == "hist" else synth.splitmix64_outputs(61 + n, n)
+    uk, out, u, err, st = run_reduce(ss, keys, vals)
+    assert err == 0
+    assert u == n
+    assert st["all_distinct"] == n
+    check(keys, vals, uk, out, u)
